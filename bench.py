@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of the GB300-native FastPM particle-mesh loop.
+
+One bench step is one whole simulation of the workload: FP64 coefficients,
+the linear field and 2LPT initial conditions at a = 0.1, every KDK step to
+a = 1 (readout + kick + drift, sort, paint, r2c FFT, force transfer, three
+c2r FFTs) and the final paint and power spectrum.  The metric is
+particle-steps/s = particles x KDK steps / time; ms per PM step is the step
+time divided by the number of KDK steps (initial conditions included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fpm|reference]
+
+N > 1 (under torchrun) runs independent replicas, one simulation per rank
+with its own seed: weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and ms/PM-step at 512³ (fwd, fwd+adjoint), % of HBM roofline"
+UNIT = "particle-steps/s"
+
+# Algorithmic (compulsory) device bytes per launch of each kernel class, as
+# (bytes per particle, bytes per mesh cell): each input read once and each
+# output written once.  Half spectra count (nc/2+1)/nc * 8 B per cell.
+def _alg_bytes(cls, N, M, nc):
+    h = 8.0 * (nc // 2 + 1) / nc            # bytes per cell of a half spectrum
+    table = {
+        "kdk_readout_kick_drift": 24 + 24 + 4 + 12 * M / N,   # dx,p r/w, key w, F read
+        "cell_keys": 12 + 4,
+        "tile_scan": 0.0,
+        "tile_scatter": 4 + 8,
+        "paint_tiles": 8 + 12 + 4 * M / N,
+        "paint_halo": 4 * M / N * 0.176,
+        "fft_z_r2c": (4 + h) * M / N,
+        "fft_y_fwd": 2 * h * M / N,
+        "fft_x_green": (h + 3 * h) * M / N,
+        "fft_y_inv": 6 * h * M / N,
+        "fft_z_c2r": (3 * h + 12) * M / N,
+    }
+    v = table.get(cls)
+    return None if v is None else v * N
+
+
+def step_algorithmic_bytes(N, M):
+    """Method minimum per PM step (60 B per particle + 44 B per cell)."""
+    return 60.0 * N + 44.0 * M
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fpm", "reference"], default="fpm")
+    ap.add_argument("--workload", choices=["large", "medium", "small"], default="large")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile-json", default=None, help="write the per-class timing here")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2010_11847_gb300 import inputs
+    return {"large": inputs.LARGE, "medium": inputs.MEDIUM, "small": inputs.SMALL}[name]
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.gpu, self.proc, self.path = gpu_index, None, None
+        self.enabled = enabled
+
+    def start(self):
+        if not self.enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = max(num(r[2]) for r in rows)
+        load = [s for s, r in zip(sm, rows) if num(r[3]) > 200.0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(nsteps_target_s=12.0, max_steps=6):
+    """The FP64 oracle's PM step (paint, force, readout, kick, drift) on a
+    128^3-particle, 128^3-mesh sub-box of the 512^3 workload (same cell size
+    1000/512 Mpc/h and particle density), repeated for ~12 s."""
+    import numpy as np
+    from oracle import fpm_oracle as O
+    from paper_2010_11847_gb300 import inputs
+    n = 128
+    box = 1000.0 * n / 512
+    wl = inputs.LARGE
+    lk = O.linear_field(inputs.white_noise(n, 7), box, wl.cosmo)
+    dx, p = O.lpt(lk, n, wl.a0, wl.cosmo)
+    stages = wl.stages()
+    times = []
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (time.perf_counter() - t0) < nsteps_target_s:
+        t = time.perf_counter()
+        dx, p = O.kdk(dx, p, stages[k:k + 2], n, n, wl.cosmo["omega_m"])
+        times.append(time.perf_counter() - t)
+        k += 1
+    ms = 1e3 * statistics.median(times)
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    return {"value": n ** 3 / (ms / 1e3), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{k} KDK steps of the FP64 numpy/scipy oracle on a 128^3-particle 128^3-mesh "
+                      f"sub-box (250 Mpc/h, same cell size and density as 512^3/1000 Mpc/h); "
+                      f"median {ms:.0f} ms per step; scipy.fft may use all host cores",
+            "ms_per_pm_step": ms}
+
+
+def run_reference(args):
+    rank, world, _ = dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import fpm_oracle as O
+    from paper_2010_11847_gb300 import inputs
+    n = 128
+    box = 1000.0 * n / 512
+    wl = inputs.LARGE
+    lk = O.linear_field(inputs.white_noise(n, 7), box, wl.cosmo)
+    dx, p = O.lpt(lk, n, wl.a0, wl.cosmo)
+    stages = wl.stages()
+    for k in range(args.warmup):
+        dx, p = O.kdk(dx, p, stages[k:k + 2], n, n, wl.cosmo["omega_m"])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        j = (args.warmup + k) % wl.nsteps
+        dx, p = O.kdk(dx, p, stages[j:j + 2], n, n, wl.cosmo["omega_m"])
+    dt = time.perf_counter() - t0
+    ms = 1e3 * dt / args.steps
+    value = n ** 3 * args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": "one oracle KDK step per bench step on a 128^3/128^3 "
+                       "sub-box at the 512^3 workload's resolution", "np": n, "nc": n, "box_mpc_h": box},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "FP64 numpy/scipy oracle, 128^3 sub-box, one KDK step per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2010_11847_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cls):
+    """DRAM bytes per launch of kernel class `cls` from the committed ncu
+    summary, when it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    e = d.get("kernels", {}).get(cls)
+    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+
+
+def run_fpm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+    rank, world, local = dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl")
+    from paper_2010_11847_gb300 import build, inputs
+    build.build()
+    from paper_2010_11847_gb300.binding import Plan, launch_count
+
+    wl = workload(args.workload)
+    N, M = wl.np_ ** 3, wl.nc ** 3
+    stages = wl.stages()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    plan = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    white_h = torch.from_numpy(inputs.white_noise(wl.np_, wl.seed + rank)).pin_memory()
+    white = white_h.to(dev)
+    lin_k = torch.empty(plan.spectrum_shape(), dtype=torch.complex64, device=dev)
+    dx = torch.empty(3, N, device=dev)
+    p = torch.empty(3, N, device=dev)
+    rho = torch.empty(wl.nc, wl.nc, wl.nc, device=dev)
+
+    def one_sim(w):
+        plan.linear_field(w, lin_k)
+        plan.lpt(lin_k, float(stages[0]), 2, dx, p)
+        plan.kdk(dx, p, stages)
+        plan.paint(dx, rho)
+        return plan.power(rho)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        one_sim(white)
+    assert plan.status() == 0, "device error flag set during warm-up"
+
+    clocks = Clocks(local, enabled=not args.no_clocks and rank == 0)
+    plan.profile(True)
+    barrier()
+    launches0 = launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_sim(white)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = launch_count() - launches0
+    prof = plan.profile_read()
+    plan.profile(False)
+    ms_total = e0.elapsed_time(e1)
+    t = torch.tensor([ms_total], device=dev)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    pm_steps = wl.nsteps
+    value = world * N * pm_steps / (ms_step / 1e3)
+    assert plan.status() == 0, "device error flag set during the timed run"
+
+    # end to end: host white noise in, density and P(k) out, every step
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.empty(wl.nc, wl.nc, wl.nc).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            w = white_h.to(dev, non_blocking=True)
+            one_sim(w)
+            rho_h.copy_(rho, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        barrier()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device=dev)
+        if world > 1:
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": world * N * pm_steps * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(white_h.numel() * 4),
+               "d2h_bytes_per_step": int(rho_h.numel() * 4 + 3 * 8 * (wl.nc // 2))}
+
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel class (device time inside the timed region)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    dominant = max((k for k in prof if _alg_bytes(k, N, M, wl.nc) is not None), key=lambda k: prof[k][0])
+    dms, dn = prof[dominant]
+    per_launch_ms = dms / dn
+    alg = _alg_bytes(dominant, N, M, wl.nc)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    step_ms = ms_step / pm_steps
+    step_alg = step_algorithmic_bytes(N, M)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
+                "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
+    cpu = None if args.no_cpu_baseline else oracle_sample()
+    breakdown = {k: {"ms_per_sim": v[0] / args.steps, "launches_per_sim": v[1] / args.steps} for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "np": wl.np_, "nc": wl.nc, "box_mpc_h": wl.box, "kdk_steps": pm_steps,
+                   "a0": wl.a0, "lpt_order": 2, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (working set several GB)",
+                   "bench_step": "one whole simulation: coefficients, linear field, 2LPT, all KDK steps, "
+                                 "final paint and P(k)"},
+        "ms_per_pm_step": step_ms,
+        "step_roofline": {"alg_bytes_per_pm_step": step_alg, "achieved_gbs": step_alg / (step_ms / 1e3) / 1e9,
+                          "frac_of_measured": step_alg / (step_ms / 1e3) / 1e9 / peak,
+                          "frac_of_8tbs_nominal": step_alg / (step_ms / 1e3) / 1e9 / 8000.0},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "breakdown": breakdown,
+    }
+    if args.profile_json:
+        json.dump(line, open(args.profile_json, "w"), indent=1)
+    print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fpm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * fpm.h -- C ABI of the GB300-native FastPM particle-mesh library (libfpm).
+ *
+ * The library computes the particle-mesh force-and-integration loop of
+ * FastPM as the FlowPM paper (Modi, Lanusse & Seljak, arXiv:2010.11847)
+ * states it: Gaussian initial conditions displaced by 2LPT (Algorithm 4),
+ * then per step a cloud-in-cell paint (Sec. 2), a real-to-complex 3D FFT,
+ * the force transfer function of Eqs. 3-5 (naive -1/k^2 Green's function,
+ * 4th-order finite-difference gradient), three complex-to-real inverse FFTs,
+ * a CIC readout and the kick/drift updates of Eqs. 1-2 with FastPM's
+ * growth-factor coefficients.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every pointer to array data is a DEVICE pointer unless stated
+ *    otherwise; the caller allocates and owns it.  A plan owns only its
+ *    scratch, twiddle and coefficient tables.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous; none synchronises the host except
+ *    fpm_status() and the calls that return host-side results as noted.
+ *  - Return value: FPM_OK (0) or a negative FPM_E* code.  Argument errors
+ *    are detected on the host before anything is launched.  Device-side
+ *    errors (a NaN or an out-of-range cell met by a kernel) set a flag in
+ *    the plan that fpm_status() reports.
+ *  - Units: displacements dx, momenta p and forces are in mesh-cell units
+ *    (x0 = box/nc = 1); time is in 1/H0.  Particle i = (ix*np + iy)*np + iz
+ *    sits on lattice node q = (ix, iy, iz) * (nc/np); its position is
+ *    q + dx (periodic).  Particle mass (nc/np)^3, so the mean density is 1.
+ *  - Particle arrays are SoA float[3][np^3] in Lagrangian order.
+ *  - Meshes are C-order float[nc][nc][nc] ([x][y][z], z fastest).
+ *  - Half spectra (lin_k) are complex64 (interleaved float pairs) in the
+ *    layout [kx][kz][ky] with kx, ky in 0..n-1 (DFT order) and kz in
+ *    0..n/2; the forward DFT is unnormalised with sign e^{-ik.x}.
+ *  - Sizes: np, nc in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512},
+ *    nc = np, 2 np or 4 np.  The cell key uses 16^3-cell tiles.
+ *  - Nothing here falls back to the CPU: without a CUDA device every call
+ *    that launches work fails with FPM_ECUDA.
+ */
+#ifndef FPM_H
+#define FPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPM_OK 0
+#define FPM_EINVAL (-1)    /* bad argument (null pointer, size, range)      */
+#define FPM_ENOMEM (-2)    /* device allocation failed                       */
+#define FPM_ECUDA (-3)     /* a CUDA runtime call or launch failed           */
+#define FPM_ETIMEOUT (-4)  /* a bounded device wait ran out                  */
+#define FPM_EDEVICE (-5)   /* device error flag: NaN / cell out of range     */
+#define FPM_ENOTIMPL (-6)  /* entry point not available in this build        */
+
+typedef struct fpm_plan fpm_plan;
+
+/* Cosmology of a flat LCDM universe (no radiation, w = -1). */
+typedef struct {
+  double omega_m, omega_b, h, n_s, sigma8, t_cmb;
+} fpm_cosmo;
+
+/* Create a plan for np^3 particles on an nc^3 mesh in a periodic box of
+ * side `box` Mpc/h.  Allocates the plan's device scratch and computes, on
+ * the GPU in FP64, the sigma8 normalisation of the Eisenstein & Hu (1998)
+ * no-wiggle power spectrum.  *plan is set only on success.  Errors:
+ * FPM_EINVAL (sizes, null, non-positive box or parameters), FPM_ENOMEM,
+ * FPM_ECUDA.  Blocks until the normalisation is computed. */
+int fpm_plan_create(fpm_plan** plan, int np, int nc, double box,
+                    const fpm_cosmo* cosmo, void* stream);
+
+/* Free the plan and its device scratch (synchronises the device). NULL ok. */
+void fpm_plan_destroy(fpm_plan* plan);
+
+/* Bytes of device scratch the plan holds. */
+int64_t fpm_plan_scratch_bytes(const fpm_plan* plan);
+
+/* Growth quantities at `n` scale factors (HOST arrays a[n] in (1e-5, 10]):
+ * out[5*i + {0..4}] = D1, D2, f1 = dlnD1/dlna, f2 = dlnD2/dlna, E = H/H0 at
+ * a[i], normalised to D1(1) = 1, D2 in units of D1_raw(1)^2 (FastPM time
+ * stepping, Sec. 2).  Computed on the GPU in FP64; `out` is a HOST array.
+ * Synchronises `stream`.  n <= 4096. */
+int fpm_growth(fpm_plan* plan, const double* a, int n, double* out, void* stream);
+
+/* Linear field, Algorithm 4 steps 1-2:
+ *   lin_k(k) = DFT(white)(k) * sqrt(P(|k|) np^3 / box^3),  lin_k(0) = 0,
+ * with P the sigma8-normalised EH no-wiggle spectrum (k = 2 pi n / box).
+ * white: float[np^3] (standard normal); lin_k: complex64 half spectrum of
+ * the np^3 lattice in the [kx][kz][ky] layout. */
+int fpm_linear_field(fpm_plan* plan, const float* white, void* lin_k, void* stream);
+
+/* Lagrangian perturbation theory at a0 (Algorithm 4 steps 3-6, order 1 or
+ * 2): dx = D1 Psi1 + D2 Psi2, p = a0^2 E (f1 D1 Psi1 + f2 D2 Psi2), with
+ * Psi1(k) = i g(k) lin_k / |w|^2, Psi2(k) = -i g(k) S(k) / |w|^2 and
+ * S = sum_{i<j} (phi_ii phi_jj - phi_ij^2), phi_ij(k) = g_i g_j lin_k / |w|^2
+ * (g the Eq. 5 gradient, w the lattice wave vector), in mesh-cell units.
+ * lin_k is read only; dx, p: float[3][np^3] written. */
+int fpm_lpt(fpm_plan* plan, const void* lin_k, double a0, int order,
+            float* dx, float* p, void* stream);
+
+/* CIC paint of the particles at q + dx (Sec. 2): rho: float[nc^3] mean 1,
+ * deterministic (fixed-point accumulation).  Optional outputs (NULL to
+ * skip): key_out uint32[np^3], the tile-major cell key of each particle
+ *   key = ((tx*NT + ty)*NT + tz)*4096 + (lx*16 + ly)*16 + lz,
+ *   cell = wrap(q + floor(dx)), t = cell/16, l = cell%16, NT = nc/16;
+ * perm_out uint32[np^3], the stable counting-sort order (by key, ties by
+ * particle index). */
+int fpm_paint(fpm_plan* plan, const float* dx, float* rho,
+              uint32_t* key_out, uint32_t* perm_out, void* stream);
+
+/* Force meshes from a density mesh (Eqs. 3-5):
+ *   F_d = IDFT( i g_d(w) * 1.5 omega_m * DFT(rho - 1) / |w|^2 ),  F(0) = 0,
+ * g_d(w) = (8 sin w_d - sin 2w_d)/6, w = 2 pi n / nc.  rho: float[nc^3];
+ * F: float[3][nc^3]. */
+int fpm_force(fpm_plan* plan, const float* rho, float* F, void* stream);
+
+/* CIC readout of three meshes at the particles: f_out[d][i] =
+ * sum_c W(q_i + dx_i - c) F[d][c].  F: float[3][nc^3]; f_out float[3][np^3]. */
+int fpm_readout(fpm_plan* plan, const float* F, const float* dx, float* f_out,
+                void* stream);
+
+/* KDK leapfrog (Eqs. 1-2) with FastPM factors over nsteps steps between the
+ * HOST scale factors a[0..nsteps] (strictly increasing, nsteps <= 2048);
+ * dx, p are updated in place (input at a[0], output at a[nsteps]).  Step k:
+ * kick a_k -> a_h (force at a_k), drift a_k -> a_{k+1} (momentum at a_h),
+ * kick a_h -> a_{k+1} (force at a_{k+1}), a_h = sqrt(a_k a_{k+1}); the
+ * closing kick of a step and the opening kick of the next are applied as
+ * one.  The coefficients are computed on the GPU in FP64.  ckpt (NULL to
+ * skip): float[nsteps+1][3][np^3], receives dx at every a_k (the momenta
+ * are not needed to reverse the steps: the force depends on dx only). */
+int fpm_kdk(fpm_plan* plan, float* dx, float* p, const double* a, int nsteps,
+            float* ckpt, void* stream);
+
+/* Binned power spectrum (Eq. 10's ingredient) of mesh field `a`, or the
+ * cross spectrum of `a` and `b` (b may be NULL):
+ *   P(k_j) = box^3/nc^6 <Re(A_k B_k^*)>,  j - 1/2 <= |n| < j + 1/2,
+ * j = 1..nc/2; HOST outputs pk[nc/2], kmean[nc/2] (h/Mpc), nmodes[nc/2]
+ * (any may be NULL).  Synchronises `stream`. */
+int fpm_power(fpm_plan* plan, const float* a, const float* b, double* pk,
+              double* kmean, double* nmodes, void* stream);
+
+/* Kernel classes of the per-class timing below. */
+#define FPM_K_KDK 0       /* CIC readout fused with kick, drift and new keys */
+#define FPM_K_KEYS 1      /* cell keys + tile histogram (first paint)        */
+#define FPM_K_SCAN 2      /* scan of the tile histogram                      */
+#define FPM_K_SCATTER 3   /* bucketing of particles by tile                  */
+#define FPM_K_PAINT 4     /* in-tile counting sort + fixed-point CIC paint   */
+#define FPM_K_HALO 5      /* tile-face sums of the paint                     */
+#define FPM_K_FFT_ZF 6    /* z pass, real-to-complex                         */
+#define FPM_K_FFT_YF 7    /* y pass, forward                                 */
+#define FPM_K_FFT_X 8     /* x pass with the Eq. 3-5 transfer function       */
+#define FPM_K_FFT_YI 9    /* y pass, inverse (3 fields)                      */
+#define FPM_K_FFT_ZI 10   /* z pass, complex-to-real (3 fields)              */
+#define FPM_K_READOUT 11  /* plain CIC readout                               */
+#define FPM_K_IC 12       /* linear field and 2LPT                           */
+#define FPM_K_COEF 13     /* FP64 growth and FastPM factors                  */
+#define FPM_K_POWER 14    /* power spectrum                                  */
+#define FPM_K_COUNT 15
+
+/* Turn per-kernel-class timing on or off for this plan (off by default).
+ * When on, every launch of the plan is bracketed by CUDA events recorded on
+ * the launching stream; this adds no synchronisation. */
+int fpm_profile(fpm_plan* plan, int enable);
+
+/* Synchronise `stream`, then return the accumulated device milliseconds and
+ * launch counts per class since the last read (ms, launches: HOST arrays
+ * of n >= FPM_K_COUNT entries), and reset them. */
+int fpm_profile_read(fpm_plan* plan, double* ms, int64_t* launches, int n, void* stream);
+
+/* Name of a kernel class (static string). */
+const char* fpm_kernel_class_name(int cls);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t fpm_launch_count(void);
+
+/* Device error flag of the plan (FPM_OK or FPM_EDEVICE / FPM_ETIMEOUT);
+ * synchronises `stream`, then clears the flag. */
+int fpm_status(fpm_plan* plan, void* stream);
+
+/* Static description of an FPM_* code. */
+const char* fpm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPM_H */

@@ -1,0 +1,230 @@
+"""Thin Python binding of libfpm's C ABI (argument marshalling only).
+
+Every method maps onto one ``fpm_*`` entry point of ``include/fpm.h`` with
+the same name.  PyTorch provides device memory and the current CUDA stream;
+all arithmetic runs in the library's CUDA kernels.  There is no CPU path:
+importing this module without the built library, or calling it without a
+CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_LIB = None
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfpm.so")
+
+FPM_OK, FPM_EINVAL, FPM_ENOMEM, FPM_ECUDA, FPM_ETIMEOUT, FPM_EDEVICE, FPM_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+
+EXPORTS = [
+    "fpm_plan_create", "fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_growth", "fpm_linear_field",
+    "fpm_lpt", "fpm_paint", "fpm_force", "fpm_readout", "fpm_kdk", "fpm_power", "fpm_status", "fpm_strerror",
+    "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count",
+]
+FPM_K_COUNT = 15
+
+
+class FpmError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        msg = lib().fpm_strerror(code).decode()
+        super().__init__(f"{fn} failed: {msg} ({code})")
+        self.code = code
+
+
+class fpm_cosmo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("omega_m", "omega_b", "h", "n_s", "sigma8", "t_cmb")]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfpm.so (built in-tree by ``build.build()``); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfpm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.fpm_plan_create.argtypes = [ctypes.POINTER(vp), i, i, d, ctypes.POINTER(fpm_cosmo), vp]
+    L.fpm_plan_destroy.argtypes = [vp]
+    L.fpm_plan_destroy.restype = None
+    L.fpm_plan_scratch_bytes.argtypes = [vp]
+    L.fpm_plan_scratch_bytes.restype = i64
+    L.fpm_growth.argtypes = [vp, vp, i, vp, vp]
+    L.fpm_linear_field.argtypes = [vp, vp, vp, vp]
+    L.fpm_lpt.argtypes = [vp, vp, d, i, vp, vp, vp]
+    L.fpm_paint.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.fpm_force.argtypes = [vp, vp, vp, vp]
+    L.fpm_readout.argtypes = [vp, vp, vp, vp, vp]
+    L.fpm_kdk.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.fpm_power.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.fpm_status.argtypes = [vp, vp]
+    L.fpm_strerror.argtypes = [i]
+    L.fpm_strerror.restype = ctypes.c_char_p
+    L.fpm_profile.argtypes = [vp, i]
+    L.fpm_profile_read.argtypes = [vp, vp, vp, i, vp]
+    L.fpm_kernel_class_name.argtypes = [i]
+    L.fpm_kernel_class_name.restype = ctypes.c_char_p
+    L.fpm_launch_count.argtypes = []
+    L.fpm_launch_count.restype = i64
+    for name in EXPORTS:
+        if name not in ("fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_strerror", "fpm_kernel_class_name",
+                        "fpm_launch_count"):
+            getattr(L, name).restype = i
+    _LIB = L
+    return L
+
+
+def _check(fn: str, code: int):
+    if code != FPM_OK:
+        raise FpmError(fn, code)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("libfpm takes contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _host_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Plan:
+    """An fpm_plan: np^3 particles on an nc^3 mesh in a periodic box (Mpc/h)."""
+
+    def __init__(self, np_: int, nc: int, box: float, cosmo: dict, stream=None):
+        import torch
+        self.np, self.nc, self.box, self.cosmo = int(np_), int(nc), float(box), dict(cosmo)
+        self.N, self.M = self.np ** 3, self.nc ** 3
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        c = fpm_cosmo(**{k: float(cosmo[k]) for k in ("omega_m", "omega_b", "h", "n_s", "sigma8", "t_cmb")})
+        h = ctypes.c_void_p()
+        _check("fpm_plan_create", lib().fpm_plan_create(ctypes.byref(h), self.np, self.nc, self.box,
+                                                         ctypes.byref(c), _stream(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fpm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # allocation helpers (torch owns the memory) ---------------------------
+    def _empty(self, *shape, dtype=None):
+        import torch
+        return torch.empty(*shape, dtype=dtype or torch.float32, device=self.device)
+
+    def spectrum_shape(self, n=None):
+        n = n or self.np
+        return (n, n // 2 + 1, n)
+
+    # entry points ----------------------------------------------------------
+    def scratch_bytes(self) -> int:
+        return int(lib().fpm_plan_scratch_bytes(self._h))
+
+    def growth(self, a, stream=None) -> np.ndarray:
+        a = _host_f64(a).ravel()
+        out = np.empty((a.size, 5))
+        _check("fpm_growth", lib().fpm_growth(self._h, a.ctypes.data, a.size, out.ctypes.data, _stream(stream)))
+        return out
+
+    def linear_field(self, white, lin_k=None, stream=None):
+        import torch
+        lin_k = lin_k if lin_k is not None else self._empty(self.spectrum_shape(), dtype=torch.complex64)
+        _check("fpm_linear_field", lib().fpm_linear_field(self._h, _ptr(white), _ptr(lin_k), _stream(stream)))
+        return lin_k
+
+    def lpt(self, lin_k, a0: float, order: int = 2, dx=None, p=None, stream=None):
+        dx = dx if dx is not None else self._empty(3, self.N)
+        p = p if p is not None else self._empty(3, self.N)
+        _check("fpm_lpt", lib().fpm_lpt(self._h, _ptr(lin_k), float(a0), int(order), _ptr(dx), _ptr(p),
+                                        _stream(stream)))
+        return dx, p
+
+    def paint(self, dx, rho=None, keys=False, perm=False, stream=None):
+        import torch
+        rho = rho if rho is not None else self._empty(self.nc, self.nc, self.nc)
+        k = self._empty(self.N, dtype=torch.int32) if keys else None
+        q = self._empty(self.N, dtype=torch.int32) if perm else None
+        _check("fpm_paint", lib().fpm_paint(self._h, _ptr(dx), _ptr(rho), _ptr(k), _ptr(q), _stream(stream)))
+        if keys or perm:
+            return rho, k, q
+        return rho
+
+    def force(self, rho, F=None, stream=None):
+        F = F if F is not None else self._empty(3, self.nc, self.nc, self.nc)
+        _check("fpm_force", lib().fpm_force(self._h, _ptr(rho), _ptr(F), _stream(stream)))
+        return F
+
+    def readout(self, F, dx, f_out=None, stream=None):
+        f_out = f_out if f_out is not None else self._empty(3, self.N)
+        _check("fpm_readout", lib().fpm_readout(self._h, _ptr(F), _ptr(dx), _ptr(f_out), _stream(stream)))
+        return f_out
+
+    def kdk(self, dx, p, a, ckpt=None, stream=None):
+        a = _host_f64(a).ravel()
+        _check("fpm_kdk", lib().fpm_kdk(self._h, _ptr(dx), _ptr(p), a.ctypes.data, a.size - 1, _ptr(ckpt),
+                                        _stream(stream)))
+        return dx, p
+
+    def power(self, a, b=None, stream=None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        nb = self.nc // 2
+        pk, km, nm = np.empty(nb), np.empty(nb), np.empty(nb)
+        _check("fpm_power", lib().fpm_power(self._h, _ptr(a), _ptr(b), pk.ctypes.data, km.ctypes.data,
+                                            nm.ctypes.data, _stream(stream)))
+        return km, pk, nm
+
+    def status(self, stream=None) -> int:
+        return int(lib().fpm_status(self._h, _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        _check("fpm_profile", lib().fpm_profile(self._h, int(bool(enable))))
+
+    def profile_read(self, stream=None) -> dict:
+        """{class name: (ms, launches)} accumulated since the last read."""
+        ms = np.zeros(FPM_K_COUNT)
+        cnt = np.zeros(FPM_K_COUNT, dtype=np.int64)
+        _check("fpm_profile_read", lib().fpm_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, FPM_K_COUNT,
+                                                          _stream(stream)))
+        return {lib().fpm_kernel_class_name(k).decode(): (float(ms[k]), int(cnt[k]))
+                for k in range(FPM_K_COUNT) if cnt[k]}
+
+    # a whole forward model (Algorithm 4 + KDK) ------------------------------
+    def simulate(self, white, a, order: int = 2, ckpt=None, stream=None):
+        lin_k = self.linear_field(white, stream=stream)
+        dx, p = self.lpt(lin_k, float(a[0]), order, stream=stream)
+        self.kdk(dx, p, a, ckpt=ckpt, stream=stream)
+        return dx, p, lin_k
+
+
+def launch_count() -> int:
+    """Kernels launched by libfpm in this process so far."""
+    return int(lib().fpm_launch_count())
+
+
+def spectrum_to_numpy_layout(spec):
+    """[kx][kz][ky] half spectrum -> numpy rfftn layout [kx][ky][kz]."""
+    return spec.permute(0, 2, 1)

@@ -1,0 +1,464 @@
+// api.cu -- the extern "C" entry points of libfpm and the plan that owns the
+// scratch.  Every entry point validates its arguments on the host, then
+// enqueues kernels on the caller's stream; nothing runs on the CPU.
+#include "internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <utility>
+#include <vector>
+
+using namespace fpm;
+
+namespace {
+std::atomic<long long> g_launches{0};
+
+// Optional per-kernel-class timing: an event pair around each launch.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> recs;   // (class, index of the start event)
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+}  // namespace
+
+struct fpm_plan {
+  int np = 0, nc = 0;
+  double box = 0;
+  CosmoParams cosmo{};
+  EhParams eh{};
+  size_t N = 0, M = 0;
+  FftTables tc, tp;            // mesh (nc) and lattice (np) tables
+  bool share_tables = false;
+  size_t specmax = 0;          // complex elements of one half spectrum
+  float2* spec = nullptr;      // 6 half spectra
+  float* real6 = nullptr;      // 6 real lattice fields (2LPT Hessian)
+  float* rho = nullptr;        // density mesh
+  float* F = nullptr;          // 3 force meshes
+  PaintCtx pc;
+  double* d_amp = nullptr;     // P(k) amplitude (sigma8 normalisation)
+  double* d_pts = nullptr;     // scale factors of a coefficient request
+  double* d_raw = nullptr;
+  double* d_gr = nullptr;
+  double* d_fac = nullptr;
+  double* d_bins = nullptr;
+  int* d_err = nullptr;
+  int64_t scratch_bytes = 0;
+  Profiler prof;
+};
+
+namespace {
+
+constexpr int MAX_STEPS = 2048;
+
+bool size_ok(int n) { return fft_size_ok(n); }
+
+template <typename T>
+int dalloc(fpm_plan* p, T** ptr, size_t count) {
+  if (count == 0) {
+    *ptr = nullptr;
+    return FPM_OK;
+  }
+  if (cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return FPM_ENOMEM;
+  }
+  p->scratch_bytes += (int64_t)(count * sizeof(T));
+  return FPM_OK;
+}
+
+void free_plan(fpm_plan* p) {
+  if (!p) return;
+  cudaFree(p->spec);
+  cudaFree(p->real6);
+  cudaFree(p->rho);
+  cudaFree(p->F);
+  cudaFree(p->pc.keys);
+  cudaFree(p->pc.items);
+  cudaFree(p->pc.tile_count);
+  cudaFree(p->pc.tile_start);
+  cudaFree(p->pc.tile_cursor);
+  cudaFree(p->pc.halo);
+  cudaFree(p->pc.big_flag);
+  cudaFree(p->d_amp);
+  cudaFree(p->d_pts);
+  cudaFree(p->d_raw);
+  cudaFree(p->d_gr);
+  cudaFree(p->d_fac);
+  cudaFree(p->d_bins);
+  cudaFree(p->d_err);
+  for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
+  if (p->tc.tw) fft_tables_destroy(&p->tc);
+  if (!p->share_tables && p->tp.tw) fft_tables_destroy(&p->tp);
+  delete p;
+}
+
+EhParams make_eh(const CosmoParams& c) {
+  // EH98 eqs. 26 and 31: sound horizon (Mpc) and the baryon suppression.
+  const double wm = c.omega_m * c.h * c.h, wb = c.omega_b * c.h * c.h, fb = c.omega_b / c.omega_m;
+  EhParams e;
+  e.h = (float)c.h;
+  e.s = (float)(44.5 * log(9.83 / wm) / sqrt(1.0 + 10.0 * pow(wb, 0.75)));
+  e.alpha = (float)(1.0 - 0.328 * log(431.0 * wm) * fb + 0.38 * log(22.3 * wm) * fb * fb);
+  e.omh = (float)(c.omega_m * c.h);
+  e.theta2 = (float)((c.t_cmb / 2.7) * (c.t_cmb / 2.7));
+  e.n_s = (float)c.n_s;
+  return e;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Copy n doubles from the host and append 1.0 (the growth normalisation point).
+int stage_points(fpm_plan* p, const double* host, int n, cudaStream_t s) {
+  std::vector<double> v(host, host + n);
+  v.push_back(1.0);
+  FPM_CUDA_TRY(cudaMemcpyAsync(p->d_pts, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  // pageable source: the copy is staged before the call returns, but keep
+  // the vector alive until the stream has consumed it
+  FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  return FPM_OK;
+}
+
+// Run one launcher (which enqueues `nk` kernels) and, when profiling,
+// bracket it with events on the same stream.
+template <typename Fn>
+int timed(fpm_plan* p, int cls, int nk, cudaStream_t s, Fn fn) {
+  size_t i0 = 0;
+  if (p->prof.on) {
+    i0 = p->prof.used;
+    cudaEvent_t a = p->prof.next();
+    if (!a || cudaEventRecord(a, s) != cudaSuccess) return FPM_ECUDA;
+  }
+  const int rc = fn();
+  g_launches += nk;
+  if (p->prof.on) {
+    cudaEvent_t b = p->prof.next();
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) return FPM_ECUDA;
+    p->prof.recs.push_back({cls, i0});
+  }
+  return rc;
+}
+
+int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s) {
+  const FftTables& t = p->tc;
+  const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
+  FPM_TRY(timed(p, FPM_K_FFT_ZF, 1, s, [&] { return fft_zfwd(t, rho, p->spec, 1, 0, 0, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_YF, 1, s, [&] { return fft_y(t, p->spec, 1, 0, false, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_X, 1, s, [&] { return fft_xforce(t, p->spec, p->spec, p->specmax, coef, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_YI, 1, s, [&] { return fft_y(t, p->spec, 3, p->specmax, true, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_ZI, 1, s, [&] { return fft_zinv(t, p->spec, F, 3, p->specmax, p->M, s); }));
+  return FPM_OK;
+}
+
+// Sort the particles (keys already in c.keys, tile histogram filled) and paint.
+int sort_paint_impl(fpm_plan* p, const PaintCtx& c, const float* dx, float* rho, uint32_t* perm, cudaStream_t s) {
+  FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
+  FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, 1, s, [&] { return launch_paint_tiles(c, dx, rho, perm, s); }));
+  if (perm) FPM_TRY(timed(p, FPM_K_PAINT, 1, s, [&] { return launch_perm_big(c, perm, s); }));
+  FPM_TRY(timed(p, FPM_K_HALO, 1, s, [&] { return launch_halo(c, rho, s); }));
+  return FPM_OK;
+}
+
+int paint_impl(fpm_plan* p, const float* dx, float* rho, uint32_t* keys, uint32_t* perm, cudaStream_t s) {
+  PaintCtx c = p->pc;
+  if (keys) c.keys = keys;
+  FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, dx, s); }));
+  return sort_paint_impl(p, c, dx, rho, perm, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fpm_strerror(int code) {
+  switch (code) {
+    case FPM_OK: return "ok";
+    case FPM_EINVAL: return "invalid argument";
+    case FPM_ENOMEM: return "device allocation failed";
+    case FPM_ECUDA: return "CUDA runtime error";
+    case FPM_ETIMEOUT: return "bounded device wait ran out";
+    case FPM_EDEVICE: return "device error flag set (non-finite or out-of-range particle)";
+    case FPM_ENOTIMPL: return "not implemented";
+    default: return "unknown error";
+  }
+}
+
+int fpm_plan_create(fpm_plan** out, int np, int nc, double box, const fpm_cosmo* cosmo, void* stream) {
+  if (!out || !cosmo) return FPM_EINVAL;
+  if (!size_ok(np) || !size_ok(nc) || nc % np != 0 || nc / np > 4 || nc % TILE != 0) return FPM_EINVAL;
+  if (!(box > 0) || !(cosmo->omega_m > 0 && cosmo->omega_m <= 1) || !(cosmo->h > 0) || !(cosmo->sigma8 > 0) ||
+      !(cosmo->omega_b >= 0 && cosmo->omega_b < cosmo->omega_m) || !(cosmo->t_cmb > 0) || !isfinite(cosmo->n_s))
+    return FPM_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return FPM_ECUDA;
+  }
+  cudaStream_t s = S(stream);
+  fpm_plan* p = new fpm_plan();
+  p->np = np;
+  p->nc = nc;
+  p->box = box;
+  p->cosmo = CosmoParams{cosmo->omega_m, cosmo->omega_b, cosmo->h, cosmo->n_s, cosmo->sigma8, cosmo->t_cmb};
+  p->eh = make_eh(p->cosmo);
+  p->N = (size_t)np * np * np;
+  p->M = (size_t)nc * nc * nc;
+  int rc = FPM_OK;
+#define TRY(x)              \
+  do {                      \
+    rc = (x);               \
+    if (rc != FPM_OK) {     \
+      free_plan(p);         \
+      return rc;            \
+    }                       \
+  } while (0)
+  TRY(paint_setup());
+  TRY(fft_tables_create(&p->tc, nc));
+  if (np == nc) {
+    p->tp = p->tc;
+    p->share_tables = true;
+  } else {
+    TRY(fft_tables_create(&p->tp, np));
+  }
+  p->specmax = spec_elems(nc);
+  TRY(dalloc(p, &p->spec, 6 * p->specmax));
+  TRY(dalloc(p, &p->real6, 6 * p->N));
+  TRY(dalloc(p, &p->rho, p->M));
+  TRY(dalloc(p, &p->F, 3 * p->M));
+  PaintCtx& c = p->pc;
+  c.g.np = np;
+  c.g.nc = nc;
+  c.g.ratio = nc / np;
+  c.g.nt = nc / TILE;
+  c.g.mass = (float)((double)(nc / np) * (nc / np) * (nc / np));
+  c.N = p->N;
+  c.M = p->M;
+  c.ntiles = c.g.nt * c.g.nt * c.g.nt;
+  TRY(dalloc(p, &c.keys, p->N));
+  TRY(dalloc(p, &c.items, p->N));
+  TRY(dalloc(p, &c.tile_count, (size_t)c.ntiles));
+  TRY(dalloc(p, &c.tile_start, (size_t)c.ntiles + 1));
+  TRY(dalloc(p, &c.tile_cursor, (size_t)c.ntiles));
+  TRY(dalloc(p, &c.halo, paint_halo_elems(c.ntiles)));
+  TRY(dalloc(p, &c.big_flag, 1));
+  TRY(dalloc(p, &p->d_amp, 1));
+  TRY(dalloc(p, &p->d_pts, 2 * MAX_STEPS + 2));
+  TRY(dalloc(p, &p->d_raw, 4 * (2 * MAX_STEPS + 2)));
+  TRY(dalloc(p, &p->d_gr, 6 * (2 * MAX_STEPS + 2)));
+  TRY(dalloc(p, &p->d_fac, 3 * MAX_STEPS));
+  TRY(dalloc(p, &p->d_bins, 3 * (size_t)(nc / 2)));
+  TRY(dalloc(p, &p->d_err, 1));
+  c.err = p->d_err;
+  if (cudaMemsetAsync(p->d_err, 0, sizeof(int), s) != cudaSuccess) TRY(FPM_ECUDA);
+  TRY(launch_sigma8(p->cosmo, p->d_amp, s));
+  g_launches += 1;
+  if (cudaStreamSynchronize(s) != cudaSuccess) TRY(FPM_ECUDA);
+#undef TRY
+  *out = p;
+  return FPM_OK;
+}
+
+void fpm_plan_destroy(fpm_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  free_plan(p);
+}
+
+int64_t fpm_plan_scratch_bytes(const fpm_plan* p) { return p ? p->scratch_bytes : 0; }
+
+int fpm_growth(fpm_plan* p, const double* a, int n, double* out, void* stream) {
+  if (!p || !a || !out || n <= 0 || n > 2 * MAX_STEPS + 1) return FPM_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!(a[i] > 1e-5 && a[i] <= 10.0)) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  FPM_TRY(stage_points(p, a, n, s));
+  FPM_TRY(timed(p, FPM_K_COEF, 2, s, [&] { return launch_growth(p->d_pts, n, p->cosmo.omega_m, p->d_raw, p->d_gr, s); }));
+  std::vector<double> rows(6 * (size_t)n);
+  FPM_CUDA_TRY(cudaMemcpyAsync(rows.data(), p->d_gr, rows.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 5; ++k) out[5 * i + k] = rows[6 * i + k];
+  return FPM_OK;
+}
+
+int fpm_linear_field(fpm_plan* p, const float* white, void* lin_k, void* stream) {
+  if (!p || !white || !lin_k) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  const FftTables& t = p->tp;
+  float2* out = reinterpret_cast<float2*>(lin_k);
+  const double n3v = (double)p->N / (p->box * p->box * p->box);
+  return timed(p, FPM_K_IC, 3, s, [&] {
+    FPM_TRY(fft_zfwd(t, white, p->spec, 1, 0, 0, s));
+    FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+    return fft_xlinear(t, p->spec, out, p->eh, p->d_amp, (float)(6.283185307179586 / p->box), (float)n3v, s);
+  });
+}
+
+int fpm_lpt(fpm_plan* p, const void* lin_k, double a0, int order, float* dx, float* mom, void* stream) {
+  if (!p || !lin_k || !dx || !mom || (order != 1 && order != 2) || !(a0 > 1e-5 && a0 <= 10.0))
+    return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  const FftTables& t = p->tp;
+  const float2* lk = reinterpret_cast<const float2*>(lin_k);
+  FPM_TRY(stage_points(p, &a0, 1, s));
+  FPM_TRY(timed(p, FPM_K_COEF, 2, s, [&] { return launch_growth(p->d_pts, 1, p->cosmo.omega_m, p->d_raw, p->d_gr, s); }));
+  const float inv_n3 = (float)(1.0 / (double)p->N);
+  const bool second = order == 2;
+  const float r = (float)(p->nc / p->np);
+  return timed(p, FPM_K_IC, second ? 11 : 4, s, [&] {
+    if (second) {
+      FPM_TRY(fft_xlpt_hessian(t, lk, p->spec, p->specmax, inv_n3, s));
+      FPM_TRY(fft_y(t, p->spec, 6, p->specmax, true, s));
+      FPM_TRY(fft_zinv(t, p->spec, p->real6, 6, p->specmax, p->N, s));
+      FPM_TRY(launch_lpt_source(p->real6, p->N, p->rho, s));
+      FPM_TRY(fft_zfwd(t, p->rho, p->spec, 1, 0, 0, s));
+      FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+    }
+    FPM_TRY(fft_xlpt_disp(t, p->spec, lk, p->spec, p->specmax, p->d_gr, (float)a0, inv_n3 * r, second, s));
+    FPM_TRY(fft_y(t, p->spec, 6, p->specmax, true, s));
+    FPM_TRY(fft_zinv(t, p->spec, dx, 3, p->specmax, p->N, s));
+    return fft_zinv(t, p->spec + 3 * p->specmax, mom, 3, p->specmax, p->N, s);
+  });
+}
+
+int fpm_paint(fpm_plan* p, const float* dx, float* rho, uint32_t* key_out, uint32_t* perm_out, void* stream) {
+  if (!p || !dx || !rho) return FPM_EINVAL;
+  return paint_impl(p, dx, rho, key_out, perm_out, S(stream));
+}
+
+int fpm_force(fpm_plan* p, const float* rho, float* F, void* stream) {
+  if (!p || !rho || !F) return FPM_EINVAL;
+  return force_impl(p, rho, F, S(stream));
+}
+
+int fpm_readout(fpm_plan* p, const float* F, const float* dx, float* f_out, void* stream) {
+  if (!p || !F || !dx || !f_out) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  return timed(p, FPM_K_READOUT, 1, s, [&] { return launch_readout(p->pc, F, dx, f_out, s); });
+}
+
+int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, float* ckpt, void* stream) {
+  if (!p || !dx || !mom || !a || nsteps < 0 || nsteps > MAX_STEPS) return FPM_EINVAL;
+  if (nsteps == 0) return FPM_OK;
+  for (int k = 0; k <= nsteps; ++k)
+    if (!(a[k] > 1e-5 && a[k] <= 10.0) || (k > 0 && !(a[k] > a[k - 1]))) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  std::vector<double> pts(a, a + nsteps + 1);
+  for (int k = 0; k < nsteps; ++k) pts.push_back(sqrt(a[k] * a[k + 1]));
+  FPM_TRY(stage_points(p, pts.data(), (int)pts.size(), s));
+  FPM_TRY(timed(p, FPM_K_COEF, 3, s, [&] {
+    return launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s);
+  }));
+  const size_t N = p->N;
+  if (ckpt) FPM_CUDA_TRY(cudaMemcpyAsync(ckpt, dx, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  FPM_TRY(paint_impl(p, dx, p->rho, nullptr, nullptr, s));
+  FPM_TRY(force_impl(p, p->rho, p->F, s));
+  for (int k = 0; k < nsteps; ++k) {
+    // closing kick of step k-1 and opening kick of step k share the force at a_k
+    const int ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
+    FPM_TRY(timed(p, FPM_K_KDK, 1, s, [&] {
+      return launch_kdk(p->pc, dx, mom, p->F, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
+    }));
+    if (ckpt)
+      FPM_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(k + 1) * 3 * N, dx, 3 * N * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s));
+    FPM_TRY(sort_paint_impl(p, p->pc, dx, p->rho, nullptr, s));
+    FPM_TRY(force_impl(p, p->rho, p->F, s));
+  }
+  return timed(p, FPM_K_KDK, 1, s, [&] {
+    return launch_kdk(p->pc, dx, mom, p->F, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
+  });
+}
+
+int fpm_power(fpm_plan* p, const float* a, const float* b, double* pk, double* kmean, double* nmodes,
+              void* stream) {
+  if (!p || !a) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  const FftTables& t = p->tc;
+  const int nb = p->nc / 2;
+  FPM_CUDA_TRY(cudaMemsetAsync(p->d_bins, 0, 3 * nb * sizeof(double), s));
+  float2* sb = b ? p->spec + p->specmax : nullptr;
+  FPM_TRY(timed(p, FPM_K_POWER, b ? 5 : 3, s, [&] {
+    FPM_TRY(fft_zfwd(t, a, p->spec, 1, 0, 0, s));
+    FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+    if (b) {
+      FPM_TRY(fft_zfwd(t, b, sb, 1, 0, 0, s));
+      FPM_TRY(fft_y(t, sb, 1, 0, false, s));
+    }
+    return fft_xpower(t, p->spec, sb, p->d_bins, s);
+  }));
+  std::vector<double> h(3 * nb);
+  FPM_CUDA_TRY(cudaMemcpyAsync(h.data(), p->d_bins, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  const double V = p->box * p->box * p->box, M = (double)p->M;
+  for (int j = 0; j < nb; ++j) {
+    const double cnt = h[nb + j];
+    if (pk) pk[j] = cnt > 0 ? V / (M * M) * h[j] / cnt : 0.0;
+    if (kmean) kmean[j] = cnt > 0 ? 6.283185307179586 / p->box * h[2 * nb + j] / cnt : 0.0;
+    if (nmodes) nmodes[j] = cnt;
+  }
+  return FPM_OK;
+}
+
+int fpm_profile(fpm_plan* p, int enable) {
+  if (!p) return FPM_EINVAL;
+  p->prof.on = enable != 0;
+  p->prof.used = 0;
+  p->prof.recs.clear();
+  return FPM_OK;
+}
+
+int fpm_profile_read(fpm_plan* p, double* ms, int64_t* launches, int n, void* stream) {
+  if (!p || !ms || !launches || n < FPM_K_COUNT) return FPM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  FPM_CUDA_TRY(cudaStreamSynchronize(S(stream)));
+  for (const auto& r : p->prof.recs) {
+    float t = 0.f;
+    FPM_CUDA_TRY(cudaEventElapsedTime(&t, p->prof.pool[r.second], p->prof.pool[r.second + 1]));
+    ms[r.first] += t;
+    launches[r.first] += 1;
+  }
+  p->prof.used = 0;
+  p->prof.recs.clear();
+  return FPM_OK;
+}
+
+const char* fpm_kernel_class_name(int cls) {
+  static const char* names[FPM_K_COUNT] = {"kdk_readout_kick_drift", "cell_keys", "tile_scan", "tile_scatter",
+                                           "paint_tiles", "paint_halo", "fft_z_r2c", "fft_y_fwd",
+                                           "fft_x_green", "fft_y_inv", "fft_z_c2r", "readout",
+                                           "initial_conditions", "coefficients_fp64", "power_spectrum"};
+  return (cls >= 0 && cls < FPM_K_COUNT) ? names[cls] : "unknown";
+}
+
+int64_t fpm_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int fpm_status(fpm_plan* p, void* stream) {
+  if (!p) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  int h = 0;
+  FPM_CUDA_TRY(cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  FPM_CUDA_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
+  if (h & ERR_TIMEOUT) return FPM_ETIMEOUT;
+  if (h) return FPM_EDEVICE;
+  return FPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// common.cuh -- shared device/host helpers of libfpm (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/fpm.h"
+
+namespace fpm {
+
+constexpr int TILE = 16;                 // cells per tile edge (cell key)
+constexpr int TILE3 = TILE * TILE * TILE;
+constexpr int TILE1 = TILE + 1;          // paint accumulator edge (tile + upper halo)
+constexpr int SHELL = 2 * TILE1 * TILE1 + 2 * (TILE - 1) * TILE1 + 2 * (TILE - 1) * (TILE - 1);
+constexpr double FIX_SCALE = 1099511627776.0;   // 2^40: fixed-point quantum of the paint
+constexpr int MAX_N = 512;
+
+// device error flag bits
+constexpr int ERR_NAN = 1;
+constexpr int ERR_RANGE = 2;
+constexpr int ERR_TIMEOUT = 4;
+
+__host__ __device__ inline bool fft_size_ok(int n) {
+  return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 ||
+         n == 256 || n == 384 || n == 512;
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by +i or -i
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// Frequency index of DFT bin j of an n-point transform: j or j - n.
+__device__ __forceinline__ int freq_of(int j, int n) { return j < n / 2 ? j : j - n; }
+
+// Geometry constants handed to kernels.
+struct Geom {
+  int np;          // particles per side
+  int nc;          // mesh cells per side
+  int ratio;       // nc / np
+  int nt;          // tiles per side (nc / 16)
+  float mass;      // (nc/np)^3
+};
+
+}  // namespace fpm
+
+// Host-side error helpers
+#define FPM_CUDA_TRY(expr)                           \
+  do {                                               \
+    cudaError_t e__ = (expr);                        \
+    if (e__ != cudaSuccess) return FPM_ECUDA;        \
+  } while (0)
+
+#define FPM_TRY(expr)                                \
+  do {                                               \
+    int r__ = (expr);                                \
+    if (r__ != FPM_OK) return r__;                   \
+  } while (0)

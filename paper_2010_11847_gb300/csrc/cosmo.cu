@@ -1,0 +1,193 @@
+// cosmo.cu -- FP64 time-stepping coefficients and sigma8 normalisation.
+//
+// The only FP64 arithmetic of the library lives here: the linear growth
+// D1, second-order growth D2, their logarithmic rates, the FastPM kick and
+// drift factors of the leapfrog (Eqs. 1-2 with the growth-factor form of
+// FastPM), and the sigma8 normalisation of the Eisenstein & Hu (1998)
+// no-wiggle spectrum.  Everything runs on the GPU so that a whole run,
+// including its coefficients, is stream-ordered.
+#include "internal.h"
+
+#include <math.h>
+
+namespace fpm {
+
+constexpr double A_INIT = 1e-5;    // growing-mode start: D1 = a, D2 = -3/7 a^2
+constexpr int RK4_STEPS = 2048;    // uniform steps in ln a
+
+struct GrowthCoef {
+  double c1, c2;   // D'' = -c1 D' + c2 (D - D1^2 for D2), c1 = 2 + dlnE/dlna, c2 = 1.5 Om(a)
+};
+
+__device__ __forceinline__ GrowthCoef growth_coef(double a, double om) {
+  const double ainv3 = 1.0 / (a * a * a);
+  const double om_a = om * ainv3 / (om * ainv3 + (1.0 - om));
+  GrowthCoef c;
+  c.c1 = 2.0 - 1.5 * om_a;
+  c.c2 = 1.5 * om_a;
+  return c;
+}
+
+__device__ __forceinline__ void growth_rhs(const GrowthCoef& c, const double* y, double* dy) {
+  dy[0] = y[1];
+  dy[1] = -c.c1 * y[1] + c.c2 * y[0];
+  dy[2] = y[3];
+  dy[3] = -c.c1 * y[3] + c.c2 * (y[2] - y[0] * y[0]);
+}
+
+// Raw growth state (D1, dD1/dlna, D2, dD2/dlna) at a_t, RK4 in ln a.
+__device__ void growth_integrate(double a_t, double om, double* y) {
+  const double h = (log(a_t) - log(A_INIT)) / RK4_STEPS;
+  const double eh = exp(h), eh2 = exp(0.5 * h);
+  double a = A_INIT;
+  y[0] = a;
+  y[1] = a;
+  y[2] = -3.0 / 7.0 * a * a;
+  y[3] = -6.0 / 7.0 * a * a;
+  GrowthCoef c0 = growth_coef(a, om);
+  for (int s = 0; s < RK4_STEPS; ++s) {
+    const GrowthCoef cm = growth_coef(a * eh2, om);
+    const GrowthCoef ce = growth_coef(a * eh, om);
+    double k1[4], k2[4], k3[4], k4[4], t[4];
+    growth_rhs(c0, y, k1);
+    for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    growth_rhs(cm, t, k2);
+    for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    growth_rhs(cm, t, k3);
+    for (int i = 0; i < 4; ++i) t[i] = y[i] + h * k3[i];
+    growth_rhs(ce, t, k4);
+    for (int i = 0; i < 4; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    a *= eh;
+    c0 = ce;
+  }
+}
+
+// One thread per scale factor a_in[0..n]; a_in[n] must be 1 (the
+// normalisation point).  raw[4*i..]: D1, dD1/dlna, D2, dD2/dlna unnormalised.
+__global__ void k_growth_raw(const double* __restrict__ a_in, int n1, double om, double* __restrict__ raw) {
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= n1) return;
+  double y[4];
+  growth_integrate(a_in[i], om, y);
+  for (int k = 0; k < 4; ++k) raw[4 * i + k] = y[k];
+}
+
+// out[6*i..]: D1, D2, f1, f2, E, dD1/da, normalised by row n (a = 1).
+__global__ void k_growth_norm(const double* __restrict__ a_in, const double* __restrict__ raw, int n,
+                              double om, double* __restrict__ out) {
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= n) return;
+  const double norm = raw[4 * n];
+  const double* y = raw + 4 * i;
+  const double a = a_in[i];
+  double* o = out + 6 * i;
+  o[0] = y[0] / norm;
+  o[1] = y[2] / (norm * norm);
+  o[2] = y[1] / y[0];
+  o[3] = y[3] / y[2];
+  o[4] = sqrt(om / (a * a * a) + (1.0 - om));
+  o[5] = y[1] / norm / a;
+}
+
+// FastPM factors from growth values at stages a_0..a_n (rows 0..n) and half
+// stages a_h (rows n+1..2n), written to fac[3*k + {0,1,2}] = kick1, drift, kick2:
+//   drift a_i->a_f, p at a_c: (D1(a_f)-D1(a_i)) / (a_c^3 E(a_c) dD1/da(a_c))
+//   kick  a_i->a_f, f at a_c: (G_f(a_f)-G_f(a_i)) / (a_c^2 E(a_c) g_f(a_c)),
+//   G_f = a^3 E dD1/da, g_f = 1.5 Om D1 / (a^2 E).
+__global__ void k_factors(const double* __restrict__ a_pts, const double* __restrict__ gr, int nsteps,
+                          double om, double* __restrict__ fac) {
+  const int k = threadIdx.x + blockIdx.x * blockDim.x;
+  if (k >= nsteps) return;
+  auto D1 = [&](int r) { return gr[6 * r + 0]; };
+  auto E = [&](int r) { return gr[6 * r + 4]; };
+  auto dD = [&](int r) { return gr[6 * r + 5]; };
+  auto A = [&](int r) { return a_pts[r]; };
+  auto Gf = [&](int r) { return A(r) * A(r) * A(r) * E(r) * dD(r); };
+  auto gf = [&](int r) { return 1.5 * om * D1(r) / (A(r) * A(r) * E(r)); };
+  const int i0 = k, i1 = k + 1, ih = nsteps + 1 + k;
+  fac[3 * k + 0] = (Gf(ih) - Gf(i0)) / (A(i0) * A(i0) * E(i0) * gf(i0));
+  fac[3 * k + 1] = (D1(i1) - D1(i0)) / (A(ih) * A(ih) * A(ih) * E(ih) * dD(ih));
+  fac[3 * k + 2] = (Gf(i1) - Gf(ih)) / (A(i1) * A(i1) * E(i1) * gf(i1));
+}
+
+// ------------------------------------------------------------ sigma8
+__device__ double eh_nowiggle_T64(double k_h, const CosmoParams& c) {
+  const double theta = c.t_cmb / 2.7;
+  const double wm = c.omega_m * c.h * c.h, wb = c.omega_b * c.h * c.h;
+  const double fb = c.omega_b / c.omega_m;
+  const double s = 44.5 * log(9.83 / wm) / sqrt(1.0 + 10.0 * pow(wb, 0.75));
+  const double alpha = 1.0 - 0.328 * log(431.0 * wm) * fb + 0.38 * log(22.3 * wm) * fb * fb;
+  const double ks = 0.43 * k_h * c.h * s;
+  const double ks2 = ks * ks;
+  const double gamma = c.omega_m * c.h * (alpha + (1.0 - alpha) / (1.0 + ks2 * ks2));
+  const double q = k_h * theta * theta / gamma;
+  const double L0 = log(2.0 * 2.718281828459045235 + 1.8 * q);
+  const double C0 = 14.2 + 731.0 / (1.0 + 62.5 * q);
+  return L0 / (L0 + C0 * q * q);
+}
+
+// sigma(8 Mpc/h)^2 of P = k^ns T^2 (unit amplitude): Simpson's rule on a
+// uniform ln k grid of SIGMA_PTS points over [1e-5, 1e2] h/Mpc.  One block;
+// a fixed-order tree reduction keeps the sum deterministic.  Writes
+// amp[0] = sigma8^2 / that integral.
+constexpr int SIGMA_PTS = 4097;
+constexpr int SIGMA_THREADS = 512;
+__global__ void __launch_bounds__(SIGMA_THREADS) k_sigma8(CosmoParams c, double* __restrict__ amp) {
+  __shared__ double part[SIGMA_THREADS];
+  const double lk0 = log(1e-5), lk1 = log(1e2);
+  const double dl = (lk1 - lk0) / (SIGMA_PTS - 1);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < SIGMA_PTS; i += SIGMA_THREADS) {
+    const double k = exp(lk0 + dl * i);
+    const double x = 8.0 * k;
+    const double w = 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+    const double T = eh_nowiggle_T64(k, c);
+    const double f = k * k * k * pow(k, c.n_s) * T * T * w * w;
+    const double sw = (i == 0 || i == SIGMA_PTS - 1) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    acc += sw * f;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = SIGMA_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sig2 = dl / 3.0 * part[0] / (2.0 * 3.14159265358979323846 * 3.14159265358979323846);
+    amp[0] = c.sigma8 * c.sigma8 / sig2;
+  }
+}
+
+// ------------------------------------------------------------ host side
+int launch_sigma8(const CosmoParams& c, double* d_amp, cudaStream_t s) {
+  k_sigma8<<<1, SIGMA_THREADS, 0, s>>>(c, d_amp);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+// d_a holds n scale factors followed by a_n = 1 (n+1 values); d_raw has
+// room for 4*(n+1) doubles; d_out receives 6*n doubles.
+int launch_growth(const double* d_a, int n, double om, double* d_raw, double* d_out, cudaStream_t s) {
+  if (n <= 0) return FPM_OK;
+  const int threads = 64;
+  k_growth_raw<<<(n + 1 + threads - 1) / threads, threads, 0, s>>>(d_a, n + 1, om, d_raw);
+  FPM_CUDA_TRY(cudaGetLastError());
+  k_growth_norm<<<(n + threads - 1) / threads, threads, 0, s>>>(d_a, d_raw, n, om, d_out);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+// d_pts holds a_0..a_n, then the half stages, then 1.0 (2n+2 values,
+// filled by the caller); d_raw / d_gr receive the raw and normalised growth
+// rows, d_fac the factors.
+int launch_factors(const double* d_pts, int nsteps, double om, double* d_raw, double* d_gr,
+                   double* d_fac, cudaStream_t s) {
+  FPM_TRY(launch_growth(d_pts, 2 * nsteps + 1, om, d_raw, d_gr, s));
+  if (nsteps > 0) {
+    k_factors<<<(nsteps + 127) / 128, 128, 0, s>>>(d_pts, d_gr, nsteps, om, d_fac);
+    FPM_CUDA_TRY(cudaGetLastError());
+  }
+  return FPM_OK;
+}
+
+}  // namespace fpm

@@ -1,0 +1,129 @@
+// fft.cu -- host launchers of the 3D FFT passes and their tables.
+#include "internal.h"
+#include "fft_passes.cuh"
+
+#include <math.h>
+#include <vector>
+
+namespace fpm {
+
+int fft_tables_create(FftTables* t, int n) {
+  t->n = n;
+  std::vector<float2> tw(n);
+  std::vector<float> g(n), w2(n);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < n; ++m) {
+    const double ang = -two_pi * m / n;
+    tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    const int f = m < n / 2 ? m : m - n;            // signed frequency
+    const double w = two_pi * f / n;
+    g[m] = (m == n / 2) ? 0.f : (float)((8.0 * sin(w) - sin(2.0 * w)) / 6.0);   // Eq. 5, 0 at Nyquist
+    w2[m] = (float)(w * w);
+  }
+  FPM_CUDA_TRY(cudaMalloc(&t->tw, n * sizeof(float2)));
+  FPM_CUDA_TRY(cudaMalloc(&t->g, n * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&t->w2, n * sizeof(float)));
+  FPM_CUDA_TRY(cudaMemcpy(t->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  FPM_CUDA_TRY(cudaMemcpy(t->g, g.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  FPM_CUDA_TRY(cudaMemcpy(t->w2, w2.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  return FPM_OK;
+}
+
+void fft_tables_destroy(FftTables* t) {
+  cudaFree(t->tw);
+  cudaFree(t->g);
+  cudaFree(t->w2);
+  t->tw = nullptr;
+  t->g = t->w2 = nullptr;
+}
+
+#define FPM_DISPATCH_N(n, CALL)            \
+  switch (n) {                             \
+    case 16: { constexpr int N = 16; CALL; } \
+    case 32: { constexpr int N = 32; CALL; } \
+    case 48: { constexpr int N = 48; CALL; } \
+    case 64: { constexpr int N = 64; CALL; } \
+    case 96: { constexpr int N = 96; CALL; } \
+    case 128: { constexpr int N = 128; CALL; } \
+    case 192: { constexpr int N = 192; CALL; } \
+    case 256: { constexpr int N = 256; CALL; } \
+    case 384: { constexpr int N = 384; CALL; } \
+    case 512: { constexpr int N = 512; CALL; } \
+    default: return FPM_EINVAL;            \
+  }
+
+template <typename K>
+static int set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    FPM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return FPM_OK;
+}
+
+template <int N>
+static int zfwd_impl(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
+                     cudaStream_t s) {
+  const size_t sm = zpass_smem<N>();
+  FPM_TRY(set_smem(k_zfwd<N>, sm));
+  dim3 grid(N * (N / (2 * ZG)), nf);
+  k_zfwd<N><<<grid, FFT_THREADS, sm, s>>>(in, spec, in_fs, out_fs, t.tw);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+template <int N>
+static int y_impl(const FftTables& t, float2* spec, int nf, size_t fs, bool inverse, cudaStream_t s) {
+  const size_t sm = ypass_smem<N>();
+  const int nlines = N * (N / 2 + 1);
+  dim3 grid((nlines + YL - 1) / YL, nf);
+  if (inverse) {
+    FPM_TRY(set_smem(k_yfft<N, true>, sm));
+    k_yfft<N, true><<<grid, FFT_THREADS, sm, s>>>(spec, nlines, fs, t.tw);
+  } else {
+    FPM_TRY(set_smem(k_yfft<N, false>, sm));
+    k_yfft<N, false><<<grid, FFT_THREADS, sm, s>>>(spec, nlines, fs, t.tw);
+  }
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+template <int N>
+static int zinv_impl(const FftTables& t, const float2* spec, float* out, int nf, size_t in_fs, size_t out_fs,
+                     cudaStream_t s) {
+  const size_t sm = zpass_smem<N>();
+  FPM_TRY(set_smem(k_zinv<N>, sm));
+  dim3 grid(N * (N / (2 * ZG)), nf);
+  k_zinv<N><<<grid, FFT_THREADS, sm, s>>>(spec, out, in_fs, out_fs, t.tw);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+template <int N>
+static int xforce_impl(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef,
+                       cudaStream_t s) {
+  const size_t sm = xpass_smem<N>(3);
+  FPM_TRY(set_smem(k_xforce<N>, sm));
+  dim3 grid((N / 2 + 1) * (N / XB));
+  k_xforce<N><<<grid, FFT_THREADS, sm, s>>>(in, out, out_fs, coef, t.tw, t.g, t.w2);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+int fft_zfwd(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
+             cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return zfwd_impl<N>(t, in, spec, nf, in_fs, out_fs, s));
+}
+
+int fft_y(const FftTables& t, float2* spec, int nf, size_t fs, bool inverse, cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return y_impl<N>(t, spec, nf, fs, inverse, s));
+}
+
+int fft_zinv(const FftTables& t, const float2* spec, float* out, int nf, size_t in_fs, size_t out_fs,
+             cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return zinv_impl<N>(t, spec, out, nf, in_fs, out_fs, s));
+}
+
+int fft_xforce(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef, cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return xforce_impl<N>(t, in, out, out_fs, coef, s));
+}
+
+}  // namespace fpm

@@ -1,0 +1,81 @@
+// internal.h -- host-side declarations shared by the translation units.
+#pragma once
+#include "common.cuh"
+
+namespace fpm {
+
+struct CosmoParams {
+  double omega_m, omega_b, h, n_s, sigma8, t_cmb;
+};
+
+// Scalars of the EH no-wiggle transfer function, precomputed on the host
+// for the per-mode FP32 evaluation.
+struct EhParams {
+  float h, s, alpha, omh, theta2, n_s;
+};
+
+// Per-size FFT tables on the device.
+struct FftTables {
+  int n = 0;
+  float2* tw = nullptr;    // exp(-2 pi i m / n), m = 0..n-1 (host FP64, rounded)
+  float* g = nullptr;      // Eq. 5 gradient (8 sin w - sin 2w)/6 of bin m, 0 at Nyquist
+  float* w2 = nullptr;     // (2 pi f / n)^2, f the signed frequency of bin m
+};
+
+// Buffers of the sort + paint pipeline.
+struct PaintCtx {
+  Geom g;
+  size_t N = 0, M = 0;
+  int ntiles = 0;
+  uint32_t* keys = nullptr;        // [N]
+  uint2* items = nullptr;          // [N] (particle, local cell) bucketed by tile
+  uint32_t* tile_count = nullptr;  // [ntiles]
+  uint32_t* tile_start = nullptr;  // [ntiles + 1]
+  uint32_t* tile_cursor = nullptr; // [ntiles]
+  long long* halo = nullptr;       // [ntiles * SHELL]
+  int* err = nullptr;
+  int* big_flag = nullptr;
+};
+
+// cosmo.cu
+int launch_sigma8(const CosmoParams& c, double* d_amp, cudaStream_t s);
+int launch_growth(const double* d_a, int n, double om, double* d_raw, double* d_out, cudaStream_t s);
+int launch_factors(const double* d_pts, int nsteps, double om, double* d_raw, double* d_gr, double* d_fac,
+                   cudaStream_t s);
+
+// fft.cu
+int fft_tables_create(FftTables* t, int n);
+void fft_tables_destroy(FftTables* t);
+int fft_zfwd(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
+             cudaStream_t s);
+int fft_y(const FftTables& t, float2* spec, int nf, size_t fs, bool inverse, cudaStream_t s);
+int fft_zinv(const FftTables& t, const float2* spec, float* out, int nf, size_t in_fs, size_t out_fs,
+             cudaStream_t s);
+int fft_xforce(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef, cudaStream_t s);
+
+// ic.cu
+int fft_xlinear(const FftTables& t, const float2* in, float2* out, const EhParams& e, const double* d_amp,
+                float kf, float n3v, cudaStream_t s);
+int fft_xlpt_hessian(const FftTables& t, const float2* lin_k, float2* out, size_t out_fs, float coef,
+                     cudaStream_t s);
+int fft_xlpt_disp(const FftTables& t, const float2* specS, const float2* lin_k, float2* out, size_t out_fs,
+                  const double* gr, float a0, float coef, bool second, cudaStream_t s);
+int fft_xpower(const FftTables& t, const float2* sa, const float2* sb, double* bins, cudaStream_t s);
+int launch_lpt_source(const float* phi, size_t n, float* S, cudaStream_t s);
+
+// paint.cu
+int paint_setup();
+size_t paint_halo_elems(int ntiles);
+int launch_keys(const PaintCtx& c, const float* dx, cudaStream_t s);
+int launch_scan(const PaintCtx& c, cudaStream_t s);
+int launch_scatter(const PaintCtx& c, cudaStream_t s);
+int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t* perm, cudaStream_t s);
+int launch_perm_big(const PaintCtx& c, uint32_t* perm, cudaStream_t s);
+int launch_halo(const PaintCtx& c, float* rho, cudaStream_t s);
+int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_out, cudaStream_t s);
+int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, const double* fac, int ik1, int ik2,
+               int idr, bool emit_keys, cudaStream_t s);
+
+inline size_t spec_elems(int n) { return (size_t)n * (n / 2 + 1) * n; }
+
+}  // namespace fpm
