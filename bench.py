@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["fpm", "reference"], default="fpm")
-    ap.add_argument("--workload", choices=["large", "medium", "small"], default="large")
+    ap.add_argument("--workload", choices=["large", "eighth", "medium", "small"], default="large")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -74,7 +74,8 @@ def parse():
 
 def workload(name):
     from paper_2010_11847_gb300 import inputs
-    return {"large": inputs.LARGE, "medium": inputs.MEDIUM, "small": inputs.SMALL}[name]
+    return {"large": inputs.LARGE, "eighth": inputs.LARGE_EIGHTH, "medium": inputs.MEDIUM,
+            "small": inputs.SMALL}[name]
 
 
 def dist():

@@ -41,6 +41,7 @@ struct fpm_plan {
   size_t N = 0, M = 0;
   FftTables tc, tp;            // mesh (nc) and lattice (np) tables
   bool share_tables = false;
+  bool f4 = false;             // internal force meshes interleaved (float4 per cell)
   size_t specmax = 0;          // complex elements of one half spectrum
   float2* spec = nullptr;      // 6 half spectra
   float* real6 = nullptr;      // 6 real lattice fields (2LPT Hessian)
@@ -151,14 +152,17 @@ int timed(fpm_plan* p, int cls, int nk, cudaStream_t s, Fn fn) {
   return rc;
 }
 
-int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s) {
+int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s, bool interleaved = false) {
   const FftTables& t = p->tc;
   const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
   FPM_TRY(timed(p, FPM_K_FFT_ZF, 1, s, [&] { return fft_zfwd(t, rho, p->spec, 1, 0, 0, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_YF, 1, s, [&] { return fft_y(t, p->spec, 1, 0, false, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_X, 1, s, [&] { return fft_xforce(t, p->spec, p->spec, p->specmax, coef, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_YI, 1, s, [&] { return fft_y(t, p->spec, 3, p->specmax, true, s); }));
-  FPM_TRY(timed(p, FPM_K_FFT_ZI, 1, s, [&] { return fft_zinv(t, p->spec, F, 3, p->specmax, p->M, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_ZI, 1, s, [&] {
+    return interleaved ? fft_zinv3(t, p->spec, reinterpret_cast<float4*>(F), p->specmax, s)
+                       : fft_zinv(t, p->spec, F, 3, p->specmax, p->M, s);
+  }));
   return FPM_OK;
 }
 
@@ -237,13 +241,10 @@ int fpm_plan_create(fpm_plan** out, int np, int nc, double box, const fpm_cosmo*
   TRY(dalloc(p, &p->spec, 6 * p->specmax));
   TRY(dalloc(p, &p->real6, 6 * p->N));
   TRY(dalloc(p, &p->rho, p->M));
-  TRY(dalloc(p, &p->F, 3 * p->M));
+  TRY(dalloc(p, &p->F, 4 * p->M));
+  p->f4 = fft_has_interleaved(nc);
   PaintCtx& c = p->pc;
-  c.g.np = np;
-  c.g.nc = nc;
-  c.g.ratio = nc / np;
-  c.g.nt = nc / TILE;
-  c.g.mass = (float)((double)(nc / np) * (nc / np) * (nc / np));
+  c.g = make_geom(np, nc);
   c.N = p->N;
   c.M = p->M;
   c.ntiles = c.g.nt * c.g.nt * c.g.nt;
@@ -365,21 +366,21 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   const size_t N = p->N;
   if (ckpt) FPM_CUDA_TRY(cudaMemcpyAsync(ckpt, dx, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   FPM_TRY(paint_impl(p, dx, p->rho, nullptr, nullptr, s));
-  FPM_TRY(force_impl(p, p->rho, p->F, s));
+  FPM_TRY(force_impl(p, p->rho, p->F, s, p->f4));
   for (int k = 0; k < nsteps; ++k) {
     // closing kick of step k-1 and opening kick of step k share the force at a_k
     const int ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
     FPM_TRY(timed(p, FPM_K_KDK, 1, s, [&] {
-      return launch_kdk(p->pc, dx, mom, p->F, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
+      return launch_kdk(p->pc, dx, mom, p->F, p->f4, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
     }));
     if (ckpt)
       FPM_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(k + 1) * 3 * N, dx, 3 * N * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s));
     FPM_TRY(sort_paint_impl(p, p->pc, dx, p->rho, nullptr, s));
-    FPM_TRY(force_impl(p, p->rho, p->F, s));
+    FPM_TRY(force_impl(p, p->rho, p->F, s, p->f4));
   }
   return timed(p, FPM_K_KDK, 1, s, [&] {
-    return launch_kdk(p->pc, dx, mom, p->F, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
+    return launch_kdk(p->pc, dx, mom, p->F, p->f4, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
   });
 }
 

@@ -12,7 +12,8 @@ constexpr int TILE = 16;                 // cells per tile edge (cell key)
 constexpr int TILE3 = TILE * TILE * TILE;
 constexpr int TILE1 = TILE + 1;          // paint accumulator edge (tile + upper halo)
 constexpr int SHELL = 2 * TILE1 * TILE1 + 2 * (TILE - 1) * TILE1 + 2 * (TILE - 1) * (TILE - 1);
-constexpr double FIX_SCALE = 1099511627776.0;   // 2^40: fixed-point quantum of the paint
+constexpr float FIX_ONE = 2147483648.0f;       // 2^31: fixed-point unit of a CIC weight
+constexpr float FIX_INV = 4.656612873077393e-10f;  // 2^-31
 constexpr int MAX_N = 512;
 
 // device error flag bits
@@ -39,6 +40,26 @@ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.
 // Frequency index of DFT bin j of an n-point transform: j or j - n.
 __device__ __forceinline__ int freq_of(int j, int n) { return j < n / 2 ? j : j - n; }
 
+// Unsigned division by a runtime constant d for n < 2^31 with a multiply:
+// m = ceil(2^(31+l) / d), l = ceil(log2 d), q = umulhi(n, m) >> (l - 1)
+// (Granlund & Montgomery 1994, round-up variant).  d >= 2.
+struct FastDiv {
+  uint32_t d, m;
+  int sh;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+  f.sh = l - 1;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return __umulhi(n, f.m) >> f.sh; }
+
 // Geometry constants handed to kernels.
 struct Geom {
   int np;          // particles per side
@@ -46,6 +67,7 @@ struct Geom {
   int ratio;       // nc / np
   int nt;          // tiles per side (nc / 16)
   float mass;      // (nc/np)^3
+  FastDiv div_np, div_np2;
 };
 
 }  // namespace fpm

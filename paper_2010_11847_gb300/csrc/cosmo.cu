@@ -13,7 +13,6 @@
 namespace fpm {
 
 constexpr double A_INIT = 1e-5;    // growing-mode start: D1 = a, D2 = -3/7 a^2
-constexpr int RK4_STEPS = 2048;    // uniform steps in ln a
 
 struct GrowthCoef {
   double c1, c2;   // D'' = -c1 D' + c2 (D - D1^2 for D2), c1 = 2 + dlnE/dlna, c2 = 1.5 Om(a)
@@ -35,21 +34,31 @@ __device__ __forceinline__ void growth_rhs(const GrowthCoef& c, const double* y,
   dy[3] = -c.c1 * y[3] + c.c2 * (y[2] - y[0] * y[0]);
 }
 
-// Raw growth state (D1, dD1/dlna, D2, dD2/dlna) at a_t, RK4 in ln a.
-__device__ void growth_integrate(double a_t, double om, double* y) {
-  const double h = (log(a_t) - log(A_INIT)) / RK4_STEPS;
-  const double eh = exp(h), eh2 = exp(0.5 * h);
-  double a = A_INIT;
-  y[0] = a;
-  y[1] = a;
-  y[2] = -3.0 / 7.0 * a * a;
-  y[3] = -6.0 / 7.0 * a * a;
-  GrowthCoef c0 = growth_coef(a, om);
-  for (int s = 0; s < RK4_STEPS; ++s) {
-    const GrowthCoef cm = growth_coef(a * eh2, om);
-    const GrowthCoef ce = growth_coef(a * eh, om);
+// One CTA per scale factor a_in[0..n]; a_in[n] must be 1 (the
+// normalisation point).  raw[4*i..]: D1, dD1/dlna, D2, dD2/dlna unnormalised.
+// The ODE coefficients at all 2*RK4_CHAIN+1 half-step points are computed
+// by the whole CTA first (they do not depend on the solution); one thread
+// then runs the dependent RK4 chain with multiply-adds only.
+constexpr int RK4_CHAIN = 1024;
+constexpr int GROWTH_THREADS = 256;
+__global__ void __launch_bounds__(GROWTH_THREADS) k_growth_raw(const double* __restrict__ a_in, double om,
+                                                               double* __restrict__ raw) {
+  __shared__ double c1[2 * RK4_CHAIN + 1], c2[2 * RK4_CHAIN + 1];
+  const double lna0 = log(A_INIT);
+  const double h = (log(a_in[blockIdx.x]) - lna0) / RK4_CHAIN;
+  for (int j = threadIdx.x; j <= 2 * RK4_CHAIN; j += blockDim.x) {
+    const GrowthCoef c = growth_coef(exp(lna0 + 0.5 * h * j), om);
+    c1[j] = c.c1;
+    c2[j] = c.c2;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double a = A_INIT;
+  double y[4] = {a, a, -3.0 / 7.0 * a * a, -6.0 / 7.0 * a * a};
+  for (int s = 0; s < RK4_CHAIN; ++s) {
+    const GrowthCoef cs{c1[2 * s], c2[2 * s]}, cm{c1[2 * s + 1], c2[2 * s + 1]}, ce{c1[2 * s + 2], c2[2 * s + 2]};
     double k1[4], k2[4], k3[4], k4[4], t[4];
-    growth_rhs(c0, y, k1);
+    growth_rhs(cs, y, k1);
     for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k1[i];
     growth_rhs(cm, t, k2);
     for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k2[i];
@@ -57,19 +66,8 @@ __device__ void growth_integrate(double a_t, double om, double* y) {
     for (int i = 0; i < 4; ++i) t[i] = y[i] + h * k3[i];
     growth_rhs(ce, t, k4);
     for (int i = 0; i < 4; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
-    a *= eh;
-    c0 = ce;
   }
-}
-
-// One thread per scale factor a_in[0..n]; a_in[n] must be 1 (the
-// normalisation point).  raw[4*i..]: D1, dD1/dlna, D2, dD2/dlna unnormalised.
-__global__ void k_growth_raw(const double* __restrict__ a_in, int n1, double om, double* __restrict__ raw) {
-  const int i = threadIdx.x + blockIdx.x * blockDim.x;
-  if (i >= n1) return;
-  double y[4];
-  growth_integrate(a_in[i], om, y);
-  for (int k = 0; k < 4; ++k) raw[4 * i + k] = y[k];
+  for (int k = 0; k < 4; ++k) raw[4 * blockIdx.x + k] = y[k];
 }
 
 // out[6*i..]: D1, D2, f1, f2, E, dD1/da, normalised by row n (a = 1).
@@ -170,7 +168,7 @@ int launch_sigma8(const CosmoParams& c, double* d_amp, cudaStream_t s) {
 int launch_growth(const double* d_a, int n, double om, double* d_raw, double* d_out, cudaStream_t s) {
   if (n <= 0) return FPM_OK;
   const int threads = 64;
-  k_growth_raw<<<(n + 1 + threads - 1) / threads, threads, 0, s>>>(d_a, n + 1, om, d_raw);
+  k_growth_raw<<<n + 1, GROWTH_THREADS, 0, s>>>(d_a, om, d_raw);
   FPM_CUDA_TRY(cudaGetLastError());
   k_growth_norm<<<(n + threads - 1) / threads, threads, 0, s>>>(d_a, d_raw, n, om, d_out);
   FPM_CUDA_TRY(cudaGetLastError());

@@ -1,6 +1,7 @@
 // fft.cu -- host launchers of the 3D FFT passes and their tables.
 #include "internal.h"
 #include "fft_passes.cuh"
+#include "fft_reg.cuh"
 
 #include <math.h>
 #include <vector>
@@ -62,6 +63,13 @@ static int set_smem(K kernel, size_t bytes) {
 template <int N>
 static int zfwd_impl(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
                      cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_zfwd_r<N>, C::SMEM));
+    k_zfwd_r<N><<<dim3(N * N / (2 * C::L), nf), C::THREADS, C::SMEM, s>>>(in, spec, in_fs, out_fs, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
   const size_t sm = zpass_smem<N>();
   FPM_TRY(set_smem(k_zfwd<N>, sm));
   dim3 grid(N * (N / (2 * ZG)), nf);
@@ -72,8 +80,21 @@ static int zfwd_impl(const FftTables& t, const float* in, float2* spec, int nf, 
 
 template <int N>
 static int y_impl(const FftTables& t, float2* spec, int nf, size_t fs, bool inverse, cudaStream_t s) {
-  const size_t sm = ypass_smem<N>();
   const int nlines = N * (N / 2 + 1);
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    dim3 grid((nlines + C::L - 1) / C::L, nf);
+    if (inverse) {
+      FPM_TRY(set_smem(k_yfft_r<N, true>, C::SMEM));
+      k_yfft_r<N, true><<<grid, C::THREADS, C::SMEM, s>>>(spec, nlines, fs, t.tw);
+    } else {
+      FPM_TRY(set_smem(k_yfft_r<N, false>, C::SMEM));
+      k_yfft_r<N, false><<<grid, C::THREADS, C::SMEM, s>>>(spec, nlines, fs, t.tw);
+    }
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  const size_t sm = ypass_smem<N>();
   dim3 grid((nlines + YL - 1) / YL, nf);
   if (inverse) {
     FPM_TRY(set_smem(k_yfft<N, true>, sm));
@@ -89,6 +110,13 @@ static int y_impl(const FftTables& t, float2* spec, int nf, size_t fs, bool inve
 template <int N>
 static int zinv_impl(const FftTables& t, const float2* spec, float* out, int nf, size_t in_fs, size_t out_fs,
                      cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_zinv_r<N>, C::SMEM));
+    k_zinv_r<N><<<dim3(N * N / (2 * C::L), nf), C::THREADS, C::SMEM, s>>>(spec, out, in_fs, out_fs, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
   const size_t sm = zpass_smem<N>();
   FPM_TRY(set_smem(k_zinv<N>, sm));
   dim3 grid(N * (N / (2 * ZG)), nf);
@@ -100,6 +128,14 @@ static int zinv_impl(const FftTables& t, const float2* spec, float* out, int nf,
 template <int N>
 static int xforce_impl(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef,
                        cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_xforce_r<N>, C::SMEM));
+    const int lines = (N / 2 + 1) * N;
+    k_xforce_r<N><<<(lines + C::L - 1) / C::L, C::THREADS, C::SMEM, s>>>(in, out, out_fs, coef, t.tw, t.g, t.w2);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
   const size_t sm = xpass_smem<N>(3);
   FPM_TRY(set_smem(k_xforce<N>, sm));
   dim3 grid((N / 2 + 1) * (N / XB));
@@ -124,6 +160,24 @@ int fft_zinv(const FftTables& t, const float2* spec, float* out, int nf, size_t 
 
 int fft_xforce(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef, cudaStream_t s) {
   FPM_DISPATCH_N(t.n, return xforce_impl<N>(t, in, out, out_fs, coef, s));
+}
+
+template <int N>
+static int zinv3_impl(const FftTables& t, const float2* spec, float4* out, size_t in_fs, cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_zinv3_r<N>, C::SMEM));
+    k_zinv3_r<N><<<N * N / (2 * C::L), C::THREADS, C::SMEM, s>>>(spec, out, in_fs, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  return FPM_ENOTIMPL;
+}
+
+bool fft_has_interleaved(int n) { return is_pow2_size(n); }
+
+int fft_zinv3(const FftTables& t, const float2* spec, float4* out, size_t in_fs, cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return zinv3_impl<N>(t, spec, out, in_fs, s));
 }
 
 }  // namespace fpm

@@ -1,0 +1,306 @@
+// fft_reg.cuh -- register-resident Stockham FFT for power-of-two lengths
+// (internal), and the hot axis passes of the force step built on it.
+//
+// A line of N points is held by T = N/8 threads, thread t owning the
+// elements t + T*s, s = 0..7 (its 8 "slots").  A stage of radix R applies
+// 8/R butterflies per thread; butterfly j = t + T*q reads slots q + (8/R)*r,
+// so the inputs of every stage are in the thread's registers.  Between two
+// stages the outputs go through shared memory once (write at the Stockham
+// position (j/Ns)*Ns*R + j%Ns + r*Ns, barrier, read back t + T*s).  The
+// last stage's outputs land exactly on the thread's own slots, so a
+// transform ends in registers in natural order: a forward transform, a
+// pointwise operator and an inverse transform chain without touching memory.
+// N = 512 = 8*8*8 needs two exchanges; twiddles come from the host FP64
+// table staged in shared memory.
+#pragma once
+#include "fft.cuh"
+#include "internal.h"
+
+namespace fpm {
+
+__device__ __forceinline__ int rp(int i) { return i + (i >> 3); }   // padded exchange index
+template <int N>
+__host__ __device__ constexpr int rline() { return N + N / 8 + 1; }   // odd: lines start on distinct banks
+
+template <int N, int R, int NS, bool INV, bool LAST>
+__device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, const float2* tw) {
+  constexpr int T = N / 8, Q = 8 / R, TWS = N / (NS * R);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + T * q;
+    const int k = (NS == 1) ? 0 : (j % NS);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[q + Q * r];
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[k * r * TWS];
+        if (INV) w.y = -w.y;
+        x[r] = cmul(x[r], w);
+      }
+    }
+    Dft<R, INV>::run(x);
+    if (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + Q * r] = x[r];
+    } else {
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[rp(base + r * NS)] = x[r];
+    }
+  }
+  if (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[s] = buf[rp(t + T * s)];
+    __syncthreads();
+  }
+}
+
+template <int N, bool INV, int NS, int... Rs>
+struct RegStages;
+template <int N, bool INV, int NS>
+struct RegStages<N, INV, NS> {
+  static __device__ __forceinline__ void run(float2 (&)[8], float2*, int, const float2*) {}
+};
+template <int N, bool INV, int NS, int R, int... Rs>
+struct RegStages<N, INV, NS, R, Rs...> {
+  static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw) {
+    reg_stage<N, R, NS, INV, sizeof...(Rs) == 0>(v, buf, t, tw);
+    RegStages<N, INV, NS * R, Rs...>::run(v, buf, t, tw);
+  }
+};
+
+template <int N>
+struct RegFft;
+#define FPM_REG_PLAN(NN, ...)                                                                  \
+  template <>                                                                                  \
+  struct RegFft<NN> {                                                                          \
+    template <bool INV>                                                                        \
+    static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw) { \
+      RegStages<NN, INV, 1, __VA_ARGS__>::run(v, buf, t, tw);                                  \
+    }                                                                                          \
+  };
+FPM_REG_PLAN(16, 8, 2)
+FPM_REG_PLAN(32, 8, 4)
+FPM_REG_PLAN(64, 8, 8)
+FPM_REG_PLAN(128, 8, 8, 2)
+FPM_REG_PLAN(256, 8, 8, 4)
+FPM_REG_PLAN(512, 8, 8, 8)
+#undef FPM_REG_PLAN
+
+__host__ __device__ constexpr bool is_pow2_size(int n) { return n >= 16 && n <= 512 && (n & (n - 1)) == 0; }
+
+// Lines per CTA: 256 threads, at least 8 lines.
+template <int N>
+struct RegCfg {
+  static constexpr int T = N / 8;
+  static constexpr int L = (256 / T) > 8 ? 256 / T : 8;
+  static constexpr int THREADS = T * L;
+  static constexpr size_t SMEM = (size_t)(L * rline<N>() + N) * sizeof(float2);
+};
+
+// ---------------------------------------------------------------- z r2c
+// L complex lines = 2L consecutive real rows (row = x*N + y) per CTA.
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zfwd_r(const float* __restrict__ in,
+                                                               float2* __restrict__ out, size_t in_fs,
+                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+  const size_t r0 = (size_t)blockIdx.x * 2 * L;
+  const float* src = in + blockIdx.y * in_fs + (r0 + 2 * g) * N;
+  float2 v[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[s] = make_float2(__ldg(src + t + T * s), __ldg(src + N + t + T * s));
+  __syncthreads();
+  float2* buf = xb + g * rline<N>();
+  RegFft<N>::template run<false>(v, buf, t, tw);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) buf[rp(t + T * s)] = v[s];
+  __syncthreads();
+  float2* dst = out + blockIdx.y * out_fs;
+  for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
+    const int kz = idx / L, gg = idx - kz * L;
+    const float2* b = xb + gg * rline<N>();
+    const float2 zk = b[rp(kz)];
+    const float2 zn = conjf2(b[rp((N - kz) & (N - 1))]);
+    const float2 A = cscale(cadd(zk, zn), 0.5f);
+    const float2 B = cscale(mul_mi(csub(zk, zn)), 0.5f);
+    const size_t row = r0 + 2 * gg;
+    const size_t x = row / N, y = row - x * N;
+    *reinterpret_cast<float4*>(dst + (x * NH + kz) * N + y) = make_float4(A.x, A.y, B.x, B.y);
+  }
+}
+
+// ---------------------------------------------------------------- y (in place, contiguous lines)
+template <int N, bool INV>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_yfft_r(float2* __restrict__ data, int nlines, size_t fs,
+                                                               const float2* __restrict__ g_tw) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const int line = threadIdx.x / T, t = threadIdx.x - line * T;
+  const int gl = blockIdx.x * L + line;
+  const bool valid = gl < nlines;
+  float2* base = data + blockIdx.y * fs + (size_t)gl * N;
+  float2 v[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[s] = valid ? base[t + T * s] : make_float2(0.f, 0.f);
+  __syncthreads();
+  RegFft<N>::template run<INV>(v, xb + line * rline<N>(), t, tw);
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) base[t + T * s] = v[s];
+  }
+}
+
+// ---------------------------------------------------------------- z c2r
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zinv_r(const float2* __restrict__ in,
+                                                               float* __restrict__ out, size_t in_fs,
+                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const size_t r0 = (size_t)blockIdx.x * 2 * L;
+  const float2* src = in + blockIdx.y * in_fs;
+  for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
+    const int kz = idx / L, gg = idx - kz * L;
+    const size_t row = r0 + 2 * gg;
+    const size_t x = row / N, y = row - x * N;
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
+    float2* b = xb + gg * rline<N>();
+    if (kz == 0 || kz == N / 2) {
+      b[rp(kz)] = make_float2(v.x, v.z);
+    } else {
+      b[rp(kz)] = make_float2(v.x - v.w, v.y + v.z);
+      b[rp(N - kz)] = make_float2(v.x + v.w, v.z - v.y);
+    }
+  }
+  __syncthreads();
+  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+  float2* buf = xb + g * rline<N>();
+  float2 v[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[s] = buf[rp(t + T * s)];
+  __syncthreads();
+  RegFft<N>::template run<true>(v, buf, t, tw);
+  float* dst = out + blockIdx.y * out_fs + (r0 + 2 * g) * N;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    dst[t + T * s] = v[s].x;
+    dst[N + t + T * s] = v[s].y;
+  }
+}
+
+// Three fields in one CTA, written interleaved as float4 (F0, F1, F2, 0)
+// per cell: the readout then fetches a CIC corner with one 16-byte load.
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
+    k_zinv3_r(const float2* __restrict__ in, float4* __restrict__ out, size_t in_fs,
+              const float2* __restrict__ g_tw) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const size_t r0 = (size_t)blockIdx.x * 2 * L;
+  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+  float2* buf = xb + g * rline<N>();
+  float2 res[3][8];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const float2* src = in + f * in_fs;
+    for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
+      const int kz = idx / L, gg = idx - kz * L;
+      const size_t row = r0 + 2 * gg;
+      const size_t x = row / N, y = row - x * N;
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
+      float2* b = xb + gg * rline<N>();
+      if (kz == 0 || kz == N / 2) {
+        b[rp(kz)] = make_float2(v.x, v.z);
+      } else {
+        b[rp(kz)] = make_float2(v.x - v.w, v.y + v.z);
+        b[rp(N - kz)] = make_float2(v.x + v.w, v.z - v.y);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) res[f][s] = buf[rp(t + T * s)];
+    __syncthreads();
+    RegFft<N>::template run<true>(res[f], buf, t, tw);
+  }
+  float4* dst = out + (r0 + 2 * g) * N;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    dst[t + T * s] = make_float4(res[0][s].x, res[1][s].x, res[2][s].x, 0.f);
+    dst[N + t + T * s] = make_float4(res[0][s].y, res[1][s].y, res[2][s].y, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- x pass: force transfer function
+// L consecutive lines l = kz*N + ky per CTA (line fastest across threads);
+// forward x transform of delta(k), then per axis d the Eq. 3-5 operator
+// F_d = i g_d coef delta / |w|^2 and the inverse x transform, from registers.
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_xforce_r(const float2* in, float2* out, size_t out_fs,
+                                                                 float coef, const float2* __restrict__ g_tw,
+                                                                 const float* __restrict__ g_g,
+                                                                 const float* __restrict__ g_w2) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
+  constexpr size_t S = (size_t)NH * N;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const int line = threadIdx.x % L, t = threadIdx.x / L;
+  const int gl = blockIdx.x * L + line;
+  const bool valid = gl < NH * N;
+  const int kz = gl / N, ky = gl - kz * N;
+  float2 d[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) d[s] = valid ? in[(size_t)(t + T * s) * S + gl] : make_float2(0.f, 0.f);
+  __syncthreads();
+  float2* buf = xb + line * rline<N>();
+  RegFft<N>::template run<false>(d, buf, t, tw);
+  const float w2yz = valid ? __ldg(g_w2 + ky) + __ldg(g_w2 + kz) : 1.f;
+  float sc[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const float k2 = __ldg(g_w2 + t + T * s) + w2yz;
+    sc[s] = k2 > 0.f ? coef / k2 : 0.f;
+  }
+  const float gy = valid ? __ldg(g_g + ky) : 0.f, gz = valid ? __ldg(g_g + kz) : 0.f;
+#pragma unroll 1
+  for (int axis = 0; axis < 3; ++axis) {
+    float2 v[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float gd = axis == 0 ? __ldg(g_g + t + T * s) : (axis == 1 ? gy : gz);
+      v[s] = mul_i(cscale(d[s], gd * sc[s]));
+    }
+    RegFft<N>::template run<true>(v, buf, t, tw);
+    if (valid) {
+      float2* o = out + axis * out_fs;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) o[(size_t)(t + T * s) * S + gl] = v[s];
+    }
+  }
+}
+
+}  // namespace fpm

@@ -28,11 +28,11 @@ struct PaintCtx {
   size_t N = 0, M = 0;
   int ntiles = 0;
   uint32_t* keys = nullptr;        // [N]
-  uint2* items = nullptr;          // [N] (particle, local cell) bucketed by tile
+  uint32_t* items = nullptr;       // [N] particle indices bucketed by tile
   uint32_t* tile_count = nullptr;  // [ntiles]
   uint32_t* tile_start = nullptr;  // [ntiles + 1]
   uint32_t* tile_cursor = nullptr; // [ntiles]
-  long long* halo = nullptr;       // [ntiles * SHELL]
+  unsigned long long* halo = nullptr;  // [ntiles * SHELL] fixed-point shell partials
   int* err = nullptr;
   int* big_flag = nullptr;
 };
@@ -52,6 +52,9 @@ int fft_y(const FftTables& t, float2* spec, int nf, size_t fs, bool inverse, cud
 int fft_zinv(const FftTables& t, const float2* spec, float* out, int nf, size_t in_fs, size_t out_fs,
              cudaStream_t s);
 int fft_xforce(const FftTables& t, const float2* in, float2* out, size_t out_fs, float coef, cudaStream_t s);
+// c2r z pass of 3 fields written interleaved (float4 per cell); pow2 sizes only.
+bool fft_has_interleaved(int n);
+int fft_zinv3(const FftTables& t, const float2* spec, float4* out, size_t in_fs, cudaStream_t s);
 
 // ic.cu
 int fft_xlinear(const FftTables& t, const float2* in, float2* out, const EhParams& e, const double* d_amp,
@@ -65,6 +68,7 @@ int launch_lpt_source(const float* phi, size_t n, float* S, cudaStream_t s);
 
 // paint.cu
 int paint_setup();
+Geom make_geom(int np, int nc);
 size_t paint_halo_elems(int ntiles);
 int launch_keys(const PaintCtx& c, const float* dx, cudaStream_t s);
 int launch_scan(const PaintCtx& c, cudaStream_t s);
@@ -73,8 +77,8 @@ int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t*
 int launch_perm_big(const PaintCtx& c, uint32_t* perm, cudaStream_t s);
 int launch_halo(const PaintCtx& c, float* rho, cudaStream_t s);
 int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_out, cudaStream_t s);
-int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, const double* fac, int ik1, int ik2,
-               int idr, bool emit_keys, cudaStream_t s);
+int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
+               int ik2, int idr, bool emit_keys, cudaStream_t s);
 
 inline size_t spec_elems(int n) { return (size_t)n * (n / 2 + 1) * n; }
 

@@ -5,38 +5,51 @@
 // cell key is computed from its float32 displacement (cell = wrap(q +
 // floor(dx)), exact in float), tile counts are histogrammed with
 // warp-aggregated atomics into an L2-resident table, scanned, and the
-// particles are bucketed by tile.  Inside a tile, a shared-memory counting
-// sort by local cell puts them in cell order (with the index tie-fix when
-// the caller asks for the permutation).
+// particles are bucketed by tile (a counting sort on the tile part of the
+// key).  When the caller asks for the permutation, a shared-memory counting
+// sort by local cell plus an index tie-fix completes the stable order.
 //
-// Paint.  One CTA per tile accumulates the CIC weights of its particles into
-// a 17^3 shared-memory block (the tile plus its upper halo) in 2^-40 fixed
-// point with int64 atomics, after summing equal-cell runs of a warp with a
-// segmented shuffle reduction.  Integer addition is associative, so the
-// density does not depend on the order of anything: it is deterministic.
+// Paint.  One CTA per tile accumulates the CIC weights of its bucket into a
+// 17^3 shared-memory block (the tile plus its upper halo).  Each weight is
+// a fixed-point fraction in units of 2^-24, added with 32-bit shared
+// atomics; a thread whose add wraps the 32-bit word (it sees it in the
+// returned old value) adds the carry to a second word, so every cell holds
+// the exact 64-bit sum.  Before adding, a warp that holds long runs of the
+// same cell merges them (segmented shuffle sums).  Integer addition is
+// associative, so the density does not depend on the order of anything: it
+// is deterministic.  The particle mass multiplies the sums at write-out.
 // Cells that only this tile touches are written directly; the shell of the
 // 17^3 block goes to a per-tile halo buffer that a second kernel sums over
-// the (up to 8) tiles that overlap each lower-face cell.
+// the (up to 8) tiles covering each face cell.
 #include "internal.h"
 
 namespace fpm {
 
-constexpr int PT_THREADS = 256;
-constexpr int PCAP = 8192;      // particles per tile sorted in shared memory
+constexpr int PB_THREADS = 512;     // paint CTA (bucket order)
+constexpr int PS_THREADS = 256;     // paint CTA (sorted order, permutation output)
+constexpr int PCAP = 8192;          // particles per tile sorted in shared memory
 constexpr int ACC = TILE1 * TILE1 * TILE1;
-constexpr size_t PAINT_SMEM = ACC * sizeof(long long) + TILE3 * sizeof(uint32_t) + PCAP * sizeof(uint32_t);
+constexpr size_t SORTED_SMEM = 2 * ACC * sizeof(uint32_t) + TILE3 * sizeof(uint32_t) + PCAP * sizeof(uint32_t);
+constexpr float W_ONE = 16777216.0f;              // 2^24: fixed-point unit of a CIC weight
+constexpr float W_INV = 5.9604644775390625e-08f;  // 2^-24
+constexpr int NFACE = TILE * TILE + (TILE - 1) * TILE + (TILE - 1) * (TILE - 1);   // 721 lower-face cells
 
+// Wrap c into [0, n) for |c| < 2^31 - n (one correction in the common case).
 __device__ __forceinline__ int wrapi(int c, int n) {
-  c %= n;
-  return c < 0 ? c + n : c;
+  if (c < 0) c += n;
+  if (c >= n) c -= n;
+  if ((unsigned)c >= (unsigned)n) {
+    c %= n;
+    if (c < 0) c += n;
+  }
+  return c;
 }
 
 __device__ __forceinline__ void lattice_node(uint32_t i, const Geom& g, int* q) {
-  const uint32_t np = g.np;
-  const uint32_t ix = i / (np * np);
-  const uint32_t rem = i - ix * np * np;
-  const uint32_t iy = rem / np;
-  const uint32_t iz = rem - iy * np;
+  const uint32_t ix = fdiv(i, g.div_np2);
+  const uint32_t rem = i - ix * g.div_np2.d;
+  const uint32_t iy = fdiv(rem, g.div_np);
+  const uint32_t iz = rem - iy * g.div_np.d;
   q[0] = ix * g.ratio;
   q[1] = iy * g.ratio;
   q[2] = iz * g.ratio;
@@ -119,36 +132,51 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* __r
 }
 
 // ---------------------------------------------------------------- bucket by tile
-__global__ void k_scatter(const uint32_t* __restrict__ keys, size_t N, uint32_t* __restrict__ cursor,
-                          uint2* __restrict__ items) {
+// Each thread places SCAT_E particles; the cursor atomics of its chunks are
+// issued back to back so their round trips to L2 overlap.
+constexpr int SCAT_E = 4;
+__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ keys, size_t N,
+                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ items) {
   const unsigned full = 0xffffffffu;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const bool active = i < N;
-  const uint32_t key = active ? keys[i] : 0u;
-  const int tile = active ? (int)(key >> 12) : -1 - lane;
-  const unsigned grp = __match_any_sync(full, tile);
-  const int leader = __ffs(grp) - 1;
-  uint32_t base = 0;
-  if (active && lane == leader) base = atomicAdd(cursor + tile, (uint32_t)__popc(grp));
-  base = __shfl_sync(full, base, leader);
-  if (active) items[base + __popc(grp & ((1u << lane) - 1u))] = make_uint2((uint32_t)i, key & 4095u);
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x * SCAT_E + threadIdx.x;
+  int tile[SCAT_E];
+  unsigned grp[SCAT_E];
+  uint32_t base[SCAT_E];
+#pragma unroll
+  for (int e = 0; e < SCAT_E; ++e) {
+    const size_t i = i0 + (size_t)e * blockDim.x;
+    tile[e] = i < N ? (int)(__ldg(keys + i) >> 12) : -1 - lane;
+    grp[e] = __match_any_sync(full, tile[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < SCAT_E; ++e) {
+    base[e] = 0;
+    if (tile[e] >= 0 && lane == __ffs(grp[e]) - 1) base[e] = atomicAdd(cursor + tile[e], (uint32_t)__popc(grp[e]));
+  }
+#pragma unroll
+  for (int e = 0; e < SCAT_E; ++e) {
+    const uint32_t b = __shfl_sync(full, base[e], __ffs(grp[e]) - 1);
+    if (tile[e] >= 0) items[b + __popc(grp[e] & ((1u << lane) - 1u))] = (uint32_t)(i0 + (size_t)e * blockDim.x);
+  }
 }
 
-// ---------------------------------------------------------------- fixed point helpers
-// w >= 0 float -> round-toward-zero of w * 2^40 as int64, using 32-bit
-// conversions only (exact split of the float into high and low words).
-__device__ __forceinline__ long long to_fix(float w) {
-  const float s = w * 1099511627776.0f;                 // * 2^40, exact
-  const float hi_f = floorf(s * 2.3283064365386963e-10f);  // / 2^32, exact
-  const float lo_f = s - hi_f * 4294967296.0f;            // exact
-  return ((long long)(int)hi_f << 32) + (long long)(unsigned)lo_f;
+// ---------------------------------------------------------------- fixed point
+__device__ __forceinline__ float from_fix(unsigned long long v, float mass) {
+  const float hi = (float)(uint32_t)(v >> 32);
+  const float lo = (float)(uint32_t)(v & 0xffffffffull);
+  return fmaf(hi, 256.0f, lo * W_INV) * mass;                // (hi 2^32 + lo) 2^-24
 }
 
-__device__ __forceinline__ float from_fix(long long v) {
-  const int hi = (int)(v >> 32);
-  const unsigned lo = (unsigned)(v & 0xffffffffll);
-  return fmaf((float)hi, 0.00390625f, (float)lo * 9.094947017729282e-13f);   // 2^-8, 2^-40
+// Exact 64-bit accumulation with 32-bit shared atomics: the thread whose
+// add wraps the low word carries into the high word.
+__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int c, uint32_t w) {
+  const uint32_t old = atomicAdd(lo + c, w);
+  if (old + w < old) atomicAdd(hi + c, 1u);
+}
+
+__device__ __forceinline__ unsigned long long acc_get(const uint32_t* lo, const uint32_t* hi, int c) {
+  return ((unsigned long long)hi[c] << 32) | lo[c];
 }
 
 __device__ __forceinline__ int shell_index(int lx, int ly, int lz) {
@@ -182,46 +210,50 @@ __device__ __forceinline__ void shell_decode(int s, int* l) {
   l[1] = 1 + s % (TILE - 1);
 }
 
-// Deposit one warp's particles.  `sorted_run` says equal local cells form
-// contiguous lane runs, so a segmented shuffle sum can merge them first.
-__device__ __forceinline__ void deposit_warp(long long* acc, bool active, int lkey, const int* l,
-                                             const float* t, float mass, bool sorted_run) {
+// Deposit one warp's particles.  When the warp holds long runs of the same
+// local cell in adjacent lanes, each run is summed first (segmented
+// shuffle reduction; a run of <= 32 weights of <= 2^24 fits 32 bits) and
+// its head lane adds the 8 corner sums; otherwise every lane adds its own.
+__device__ __forceinline__ void deposit_warp(uint32_t* lo, uint32_t* hi, bool active, const int* l,
+                                             const float* t) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  long long w[8];
+  uint32_t w[8];
   {
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float v = mass * wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1];
-      w[c] = active ? to_fix(v) : 0ll;
-    }
+    for (int c = 0; c < 8; ++c)
+      w[c] = active ? __float2uint_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * W_ONE) : 0u;
   }
-  bool lead = active;
-  if (sorted_run) {
-    const unsigned grp = __match_any_sync(full, active ? lkey : -1 - lane);
-    if (__any_sync(full, __popc(grp) > 1)) {
-      const int last = 31 - __clz(grp);
+  const int key = active ? (l[0] * TILE + l[1]) * TILE + l[2] : -1 - lane;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const bool head = (lane == 0) || (prev != key);
+  const unsigned heads = __ballot_sync(full, head);
+  const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
+  if (__popc(heads) > 24) {
+    if (active) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        long long v = w[c];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const long long o = __shfl_down_sync(full, v, off);
-          if (lane + off <= last) v += o;
-        }
-        w[c] = v;
-      }
+      for (int c = 0; c < 8; ++c)
+        acc_add(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
     }
-    lead = active && (lane == __ffs(grp) - 1);
+    return;
   }
-  if (lead) {
-    const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
+  const unsigned after = heads & ~((2u << lane) - 1u);
+  const int seg_end = after ? __ffs(after) - 1 : 32;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int off = (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1);
-      atomicAdd(reinterpret_cast<unsigned long long*>(acc + base + off), (unsigned long long)w[c]);
+  for (int c = 0; c < 8; ++c) {
+    uint32_t s = w[c];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o = __shfl_down_sync(full, s, off);
+      if (lane + off < seg_end) s += o;
     }
+    w[c] = s;
+  }
+  if (active && head) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      acc_add(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
   }
 }
 
@@ -242,32 +274,87 @@ __device__ __forceinline__ bool particle_local(const float* __restrict__ dx, siz
   return ok;
 }
 
-template <bool PERM>
-__global__ void __launch_bounds__(PT_THREADS) k_paint_tiles(const float* __restrict__ dx, size_t N,
-                                                            const uint2* __restrict__ items,
-                                                            const uint32_t* __restrict__ tile_start, Geom g,
-                                                            float* __restrict__ rho, long long* __restrict__ halo,
-                                                            uint32_t* __restrict__ perm, int* __restrict__ err,
-                                                            int* __restrict__ big_flag) {
-  extern __shared__ unsigned char smraw[];
-  long long* acc = reinterpret_cast<long long*>(smraw);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(acc + ACC);
-  uint32_t* sorted = hist + TILE3;
+// Write the tile's interior cells (final) and its 17^3 shell (partials).
+__device__ __forceinline__ void paint_writeout(const uint32_t* lo, const uint32_t* hi, const int* o, int tile,
+                                               const Geom& g, float* __restrict__ rho,
+                                               unsigned long long* __restrict__ halo) {
+  const int nc = g.nc;
+  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
+    const int lx = 1 + k / ((TILE - 1) * (TILE - 1));
+    const int ly = 1 + (k / (TILE - 1)) % (TILE - 1);
+    const int lz = 1 + k % (TILE - 1);
+    rho[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
+        from_fix(acc_get(lo, hi, (lx * TILE1 + ly) * TILE1 + lz), g.mass);
+  }
+  unsigned long long* hb = halo + (size_t)tile * SHELL;
+  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
+    int l[3];
+    shell_decode(s, l);
+    hb[s] = acc_get(lo, hi, (l[0] * TILE1 + l[1]) * TILE1 + l[2]);
+  }
+}
+
+// Hot-path paint: one CTA per tile, particles in bucket order.
+__global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,
+                                                             const uint32_t* __restrict__ items,
+                                                             const uint32_t* __restrict__ tile_start, Geom g,
+                                                             float* __restrict__ rho,
+                                                             unsigned long long* __restrict__ halo,
+                                                             int* __restrict__ err) {
+  __shared__ uint32_t lo[ACC], hi[ACC];
   const int nt = g.nt;
-  const int tid = blockIdx.x;
-  const int o[3] = {(tid / (nt * nt)) * TILE, ((tid / nt) % nt) * TILE, (tid % nt) * TILE};
-  const uint32_t s0 = tile_start[tid], s1 = tile_start[tid + 1];
+  const int tile = blockIdx.x;
+  const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
+  const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
   const int n = (int)(s1 - s0);
-  for (int k = threadIdx.x; k < ACC; k += blockDim.x) acc[k] = 0;
+  for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
+  __syncthreads();
+  bool bad = false;
+  const int nw = (n + 31) & ~31;
+  for (int k = threadIdx.x; k < nw; k += blockDim.x) {
+    const bool active = k < n;
+    int l[3] = {0, 0, 0};
+    float t[3] = {0.f, 0.f, 0.f};
+    if (active) bad |= !particle_local(dx, N, __ldg(items + s0 + k), g, o, l, t);
+    deposit_warp(lo, hi, active, l, t);
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+  __syncthreads();
+  paint_writeout(lo, hi, o, tile, g, rho, halo);
+}
+
+// Paint with the permutation output: counting sort of the tile's bucket by
+// local cell in shared memory, index tie-fix, then the same deposit in
+// sorted order.  Tiles larger than PCAP are deposited in bucket order and
+// sorted by k_perm_big.
+__global__ void __launch_bounds__(PS_THREADS) k_paint_sorted(const float* __restrict__ dx, size_t N,
+                                                             const uint32_t* __restrict__ items,
+                                                             const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ tile_start, Geom g,
+                                                             float* __restrict__ rho,
+                                                             unsigned long long* __restrict__ halo,
+                                                             uint32_t* __restrict__ perm, int* __restrict__ err) {
+  extern __shared__ uint32_t smraw[];
+  uint32_t* lo = smraw;
+  uint32_t* hi = lo + ACC;
+  uint32_t* hist = hi + ACC;
+  uint32_t* sorted = hist + TILE3;
+  __shared__ uint32_t part[PS_THREADS];
+  const int nt = g.nt;
+  const int tile = blockIdx.x;
+  const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
+  const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
+  const int n = (int)(s1 - s0);
+  for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
   for (int k = threadIdx.x; k < TILE3; k += blockDim.x) hist[k] = 0;
   __syncthreads();
   bool bad = false;
+  const int nw = (n + 31) & ~31;
   if (n <= PCAP) {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) atomicAdd(hist + items[s0 + k].y, 1u);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) atomicAdd(hist + (keys[items[s0 + k]] & 4095u), 1u);
     __syncthreads();
     {   // exclusive scan of the 4096 local-cell counts: 16 per thread
-      constexpr int PER = TILE3 / PT_THREADS;
-      __shared__ uint32_t part[PT_THREADS];
+      constexpr int PER = TILE3 / PS_THREADS;
       uint32_t loc[PER];
       uint32_t s = 0;
       for (int k = 0; k < PER; ++k) {
@@ -276,7 +363,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_paint_tiles(const float* __restr
       }
       part[threadIdx.x] = s;
       __syncthreads();
-      for (int off = 1; off < PT_THREADS; off <<= 1) {
+      for (int off = 1; off < PS_THREADS; off <<= 1) {
         const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
         __syncthreads();
         part[threadIdx.x] += v;
@@ -290,99 +377,101 @@ __global__ void __launch_bounds__(PT_THREADS) k_paint_tiles(const float* __restr
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const uint2 it = items[s0 + k];
-      sorted[atomicAdd(hist + it.y, 1u)] = it.x;
+      const uint32_t i = items[s0 + k];
+      sorted[atomicAdd(hist + (keys[i] & 4095u), 1u)] = i;
     }
     __syncthreads();
-    if (PERM) {   // order equal cells by particle index (hist[c] is now the end of cell c)
-      for (int c = threadIdx.x; c < TILE3; c += blockDim.x) {
-        const int lo = c ? (int)hist[c - 1] : 0, hi = (int)hist[c];
-        for (int a = lo + 1; a < hi; ++a) {
-          const uint32_t v = sorted[a];
-          int b = a - 1;
-          while (b >= lo && sorted[b] > v) {
-            sorted[b + 1] = sorted[b];
-            --b;
-          }
-          sorted[b + 1] = v;
+    // order equal cells by particle index (hist[c] is now the end of cell c)
+    for (int c = threadIdx.x; c < TILE3; c += blockDim.x) {
+      const int lo = c ? (int)hist[c - 1] : 0, hi = (int)hist[c];
+      for (int a = lo + 1; a < hi; ++a) {
+        const uint32_t v = sorted[a];
+        int b = a - 1;
+        while (b >= lo && sorted[b] > v) {
+          sorted[b + 1] = sorted[b];
+          --b;
         }
+        sorted[b + 1] = v;
       }
-      __syncthreads();
-      for (int k = threadIdx.x; k < n; k += blockDim.x) perm[s0 + k] = sorted[k];
     }
-    const int nw = (n + 31) & ~31;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) perm[s0 + k] = sorted[k];
     for (int k = threadIdx.x; k < nw; k += blockDim.x) {
       const bool active = k < n;
       int l[3] = {0, 0, 0};
       float t[3] = {0.f, 0.f, 0.f};
       if (active) bad |= !particle_local(dx, N, sorted[k], g, o, l, t);
-      const int lkey = (l[0] * TILE + l[1]) * TILE + l[2];
-      deposit_warp(acc, active, lkey, l, t, g.mass, true);
+      deposit_warp(lo, hi, active, l, t);
     }
   } else {
-    if (PERM && threadIdx.x == 0) atomicOr(big_flag, 1);
-    const int nw = (n + 31) & ~31;
     for (int k = threadIdx.x; k < nw; k += blockDim.x) {
       const bool active = k < n;
       int l[3] = {0, 0, 0};
       float t[3] = {0.f, 0.f, 0.f};
-      if (active) bad |= !particle_local(dx, N, items[s0 + k].x, g, o, l, t);
-      deposit_warp(acc, active, 0, l, t, g.mass, false);
+      if (active) bad |= !particle_local(dx, N, items[s0 + k], g, o, l, t);
+      deposit_warp(lo, hi, active, l, t);
     }
   }
   if (bad) atomicOr(err, ERR_RANGE);
   __syncthreads();
-  // interior cells: final
-  const int nc = g.nc;
-  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
-    const int lx = 1 + k / ((TILE - 1) * (TILE - 1));
-    const int ly = 1 + (k / (TILE - 1)) % (TILE - 1);
-    const int lz = 1 + k % (TILE - 1);
-    rho[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
-        from_fix(acc[(lx * TILE1 + ly) * TILE1 + lz]);
-  }
-  long long* hb = halo + (size_t)tid * SHELL;
-  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
-    int l[3];
-    shell_decode(s, l);
-    hb[s] = acc[(l[0] * TILE1 + l[1]) * TILE1 + l[2]];
-  }
+  paint_writeout(lo, hi, o, tile, g, rho, halo);
 }
 
 // Lower-face cells of every tile: sum the shell partials of the up to 8
-// tiles whose 17^3 blocks cover the cell.
-__global__ void k_paint_halo(const long long* __restrict__ halo, Geom g, float* __restrict__ rho) {
+// tiles whose 17^3 blocks cover the cell.  One thread per face cell.
+__global__ void __launch_bounds__(768) k_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
+                                                    float* __restrict__ rho) {
+  __shared__ uint32_t nb[8];
   const int nt = g.nt, nc = g.nc;
-  const int tid = blockIdx.x;
-  const int tc[3] = {tid / (nt * nt), (tid / nt) % nt, tid % nt};
-  for (int k = threadIdx.x; k < TILE3; k += blockDim.x) {
-    const int l[3] = {k >> 8, (k >> 4) & 15, k & 15};
-    if (l[0] && l[1] && l[2]) continue;
-    long long sum = 0;
-    for (int b = 0; b < 8; ++b) {
-      const int bb[3] = {b >> 2, (b >> 1) & 1, b & 1};
-      bool ok = true;
-      for (int d = 0; d < 3; ++d) ok &= !(bb[d] && l[d]);
-      if (!ok) continue;
-      const int st = ((wrapi(tc[0] - bb[0], nt)) * nt + wrapi(tc[1] - bb[1], nt)) * nt + wrapi(tc[2] - bb[2], nt);
-      sum += halo[(size_t)st * SHELL + shell_index(l[0] + TILE * bb[0], l[1] + TILE * bb[1], l[2] + TILE * bb[2])];
-    }
-    rho[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] = from_fix(sum);
+  const int tile = blockIdx.x;
+  const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
+  if (threadIdx.x < 8) {
+    const int b = threadIdx.x;
+    const int x = tc[0] - (b >> 2), y = tc[1] - ((b >> 1) & 1), z = tc[2] - (b & 1);
+    nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
   }
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k >= NFACE) return;
+  int l[3];
+  if (k < TILE * TILE) {
+    l[0] = 0;
+    l[1] = k >> 4;
+    l[2] = k & 15;
+  } else if (k < TILE * TILE + (TILE - 1) * TILE) {
+    const int r = k - TILE * TILE;
+    l[0] = 1 + (r >> 4);
+    l[1] = 0;
+    l[2] = r & 15;
+  } else {
+    const int r = k - TILE * TILE - (TILE - 1) * TILE;
+    l[0] = 1 + r / (TILE - 1);
+    l[1] = 1 + r % (TILE - 1);
+    l[2] = 0;
+  }
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
+    if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
+    sum += halo[(size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz)];
+  }
+  rho[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
+      from_fix(sum, g.mass);
 }
 
 // Stable order of one oversized tile for the permutation output: counting
 // sort by local cell with a global cursor table, then the index tie-fix.
-// One CTA per tile; only launched when some tile exceeded PCAP.
-__global__ void k_perm_big(const uint2* __restrict__ items, const uint32_t* __restrict__ tile_start,
-                           uint32_t* __restrict__ perm) {
+// One CTA per tile; tiles within PCAP return at once.
+__global__ void k_perm_big(const uint32_t* __restrict__ items, const uint32_t* __restrict__ keys,
+                           const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ perm) {
   __shared__ uint32_t cur[TILE3];
-  const int tid = blockIdx.x;
-  const uint32_t s0 = tile_start[tid], s1 = tile_start[tid + 1];
+  const int tile = blockIdx.x;
+  const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
   if ((int)(s1 - s0) <= PCAP) return;
   for (int k = threadIdx.x; k < TILE3; k += blockDim.x) cur[k] = 0;
   __syncthreads();
-  for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) atomicAdd(cur + items[k].y, 1u);
+  for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) atomicAdd(cur + (keys[items[k]] & 4095u), 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = s0;
@@ -394,8 +483,8 @@ __global__ void k_perm_big(const uint2* __restrict__ items, const uint32_t* __re
   }
   __syncthreads();
   for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-    const uint2 it = items[k];
-    perm[atomicAdd(cur + it.y, 1u)] = it.x;
+    const uint32_t i = items[k];
+    perm[atomicAdd(cur + (keys[i] & 4095u), 1u)] = i;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < TILE3; c += blockDim.x) {
@@ -415,68 +504,132 @@ __global__ void k_perm_big(const uint2* __restrict__ items, const uint32_t* __re
 // ---------------------------------------------------------------- readout (+ kick, drift)
 // f_i = sum_c W(x_i - c) F_c.  With KDK: p += K f, dx += D p, then the new
 // cell key and tile histogram of the drifted particle.
-template <bool KDK>
-__global__ void k_readout(float* __restrict__ dx, float* __restrict__ p, const float* __restrict__ F, Geom g,
-                          size_t N, size_t M, const double* __restrict__ fac, int ik1, int ik2, int idr,
-                          float* __restrict__ f_out, uint32_t* __restrict__ keys,
-                          uint32_t* __restrict__ tile_count, int* __restrict__ err) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < N;
+// Force at CIC corner `idx`: three separate meshes, or interleaved float4.
+template <bool F4>
+__device__ __forceinline__ void corner_force(const float* __restrict__ F, size_t M, size_t idx, float w,
+                                             float* f) {
+  if (F4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(F) + idx);
+    f[0] = fmaf(w, v.x, f[0]);
+    f[1] = fmaf(w, v.y, f[1]);
+    f[2] = fmaf(w, v.z, f[2]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = fmaf(w, __ldg(F + a * M + idx), f[a]);
+  }
+}
+
+template <bool KDK, bool F4>
+__global__ void __launch_bounds__(256) k_readout(float* __restrict__ dx, float* __restrict__ p,
+                                                 const float* __restrict__ F, Geom g, size_t N, size_t M,
+                                                 const double* __restrict__ fac, int ik1, int ik2, int idr,
+                                                 float* __restrict__ f_out, uint32_t* __restrict__ keys,
+                                                 uint32_t* __restrict__ tile_count, int* __restrict__ err,
+                                                 int iters) {
+  // each CTA walks a contiguous chunk of iters*256 particles, so that the
+  // force rows its neighbouring lattice rows share stay in its L1; the next
+  // chunk's dx and p are fetched while the current one gathers its forces
   const int nc = g.nc;
-  int tile = 0;
-  if (active) {
-    int q[3], c[3];
-    float t[3], d[3];
-    lattice_node((uint32_t)i, g, q);
-    bool ok = true;
-    for (int a = 0; a < 3; ++a) {
-      d[a] = dx[a * N + i];
-      ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-    }
-    int c1[3];
-    for (int a = 0; a < 3; ++a) c1[a] = (c[a] + 1 == nc) ? 0 : c[a] + 1;
-    float f[3] = {0.f, 0.f, 0.f};
+  float K = 0.f, D = 0.f;
+  if (KDK) {
+    K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
+    D = idr >= 0 ? (float)fac[idr] : 0.f;
+  }
+  const size_t c0 = (size_t)blockIdx.x * iters * blockDim.x;
+  float dn[3] = {0.f, 0.f, 0.f}, pn[3] = {0.f, 0.f, 0.f};
+  {
+    const size_t i = c0 + threadIdx.x;
+    if (i < N) {
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int cx = (b & 4) ? c1[0] : c[0], cy = (b & 2) ? c1[1] : c[1], cz = (b & 1) ? c1[2] : c[2];
-      const float w = ((b & 4) ? t[0] : 1.f - t[0]) * ((b & 2) ? t[1] : 1.f - t[1]) * ((b & 1) ? t[2] : 1.f - t[2]);
-      const size_t idx = ((size_t)cx * nc + cy) * nc + cz;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) f[a] = fmaf(w, __ldg(F + a * M + idx), f[a]);
-    }
-    if (!KDK) {
-      for (int a = 0; a < 3; ++a) f_out[a * N + i] = f[a];
-      if (!ok) atomicOr(err, ERR_NAN);
-    } else {
-      const float K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
-      const float D = idr >= 0 ? (float)fac[idr] : 0.f;
       for (int a = 0; a < 3; ++a) {
-        const float pa = fmaf(K, f[a], p[a * N + i]);
-        p[a * N + i] = pa;
-        d[a] = fmaf(D, pa, d[a]);
-        dx[a * N + i] = d[a];
+        dn[a] = dx[a * N + i];
+        if (KDK) pn[a] = p[a * N + i];
       }
-      if (keys) {
-        for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-        const uint32_t key = tile_key(c, g.nt);
-        keys[i] = key;
-        tile = key >> 12;
-      }
-      if (!ok) atomicOr(err, ERR_NAN);
     }
   }
-  if (KDK && keys) warp_count(tile_count, tile, active);
+  for (int it = 0; it < iters; ++it) {
+    if (c0 + (size_t)it * blockDim.x >= N) break;
+    const size_t i = c0 + (size_t)it * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    float d[3] = {dn[0], dn[1], dn[2]}, pp[3] = {pn[0], pn[1], pn[2]};
+    const size_t inext = i + blockDim.x;
+    if (it + 1 < iters && inext < N) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dn[a] = dx[a * N + inext];
+        if (KDK) pn[a] = p[a * N + inext];
+      }
+    }
+    int tile = 0;
+    if (active) {
+      int q[3], c[3];
+      float t[3];
+      lattice_node((uint32_t)i, g, q);
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+      const int cx1 = (c[0] + 1 == nc) ? 0 : c[0] + 1;
+      const int cy1 = (c[1] + 1 == nc) ? 0 : c[1] + 1;
+      const int cz1 = (c[2] + 1 == nc) ? 0 : c[2] + 1;
+      const size_t rx[2] = {(size_t)c[0] * nc * nc, (size_t)cx1 * nc * nc};
+      const int ry[2] = {c[1] * nc, cy1 * nc};
+      const int rz[2] = {c[2], cz1};
+      const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+      float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        corner_force<F4>(F, M, rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1],
+                         wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1], f);
+      if (!KDK) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f_out[a * N + i] = f[a];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float pa = fmaf(K, f[a], pp[a]);
+          p[a * N + i] = pa;
+          d[a] = fmaf(D, pa, d[a]);
+          dx[a * N + i] = d[a];
+        }
+        if (keys) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+          const uint32_t key = tile_key(c, g.nt);
+          keys[i] = key;
+          tile = key >> 12;
+        }
+      }
+      if (!ok) atomicOr(err, ERR_NAN);
+    }
+    if (KDK && keys) warp_count(tile_count, tile, active);
+  }
+}
+
+// Chunks per CTA for the readout: long chunks at scale, at least ~8 CTAs per SM.
+static int readout_iters(size_t N) {
+  const size_t per = N / (256 * 152 * 8);
+  return (int)(per < 1 ? 1 : (per > 8 ? 8 : per));
 }
 
 // ---------------------------------------------------------------- host side
 static int grid_of(size_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 int paint_setup() {
-  FPM_CUDA_TRY(cudaFuncSetAttribute(k_paint_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)PAINT_SMEM));
-  FPM_CUDA_TRY(cudaFuncSetAttribute(k_paint_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)PAINT_SMEM));
+  FPM_CUDA_TRY(cudaFuncSetAttribute(k_paint_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SORTED_SMEM));
   return FPM_OK;
+}
+
+Geom make_geom(int np, int nc) {
+  Geom g;
+  g.np = np;
+  g.nc = nc;
+  g.ratio = nc / np;
+  g.nt = nc / TILE;
+  g.mass = (float)((double)(nc / np) * (nc / np) * (nc / np));
+  g.div_np = make_fastdiv((uint32_t)np);
+  g.div_np2 = make_fastdiv((uint32_t)np * (uint32_t)np);
+  return g;
 }
 
 size_t paint_halo_elems(int ntiles) { return (size_t)ntiles * SHELL; }
@@ -495,48 +648,55 @@ int launch_scan(const PaintCtx& c, cudaStream_t s) {
 }
 
 int launch_scatter(const PaintCtx& c, cudaStream_t s) {
-  k_scatter<<<grid_of(c.N, 256), 256, 0, s>>>(c.keys, c.N, c.tile_cursor, c.items);
+  k_scatter<<<grid_of(c.N, 256 * SCAT_E), 256, 0, s>>>(c.keys, c.N, c.tile_cursor, c.items);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
 int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t* perm, cudaStream_t s) {
   if (perm) {
-    FPM_CUDA_TRY(cudaMemsetAsync(c.big_flag, 0, sizeof(int), s));
-    k_paint_tiles<true><<<c.ntiles, PT_THREADS, PAINT_SMEM, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho,
-                                                                  c.halo, perm, c.err, c.big_flag);
+    k_paint_sorted<<<c.ntiles, PS_THREADS, SORTED_SMEM, s>>>(dx, c.N, c.items, c.keys, c.tile_start, c.g, rho,
+                                                              c.halo, perm, c.err);
   } else {
-    k_paint_tiles<false><<<c.ntiles, PT_THREADS, PAINT_SMEM, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho,
-                                                                   c.halo, nullptr, c.err, c.big_flag);
+    k_paint_bucket<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo, c.err);
   }
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
 int launch_perm_big(const PaintCtx& c, uint32_t* perm, cudaStream_t s) {
-  k_perm_big<<<c.ntiles, 256, 0, s>>>(c.items, c.tile_start, perm);
+  k_perm_big<<<c.ntiles, 256, 0, s>>>(c.items, c.keys, c.tile_start, perm);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
 int launch_halo(const PaintCtx& c, float* rho, cudaStream_t s) {
-  k_paint_halo<<<c.ntiles, 256, 0, s>>>(c.halo, c.g, rho);
+  k_paint_halo<<<c.ntiles, 768, 0, s>>>(c.halo, c.g, rho);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
 int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_out, cudaStream_t s) {
-  k_readout<false><<<grid_of(c.N, 256), 256, 0, s>>>(const_cast<float*>(dx), nullptr, F, c.g, c.N, c.M,
-                                                     nullptr, -1, -1, -1, f_out, nullptr, nullptr, c.err);
+  const int it = readout_iters(c.N);
+  k_readout<false, false><<<grid_of(c.N, 256 * it), 256, 0, s>>>(const_cast<float*>(dx), nullptr, F, c.g, c.N,
+                                                                 c.M, nullptr, -1, -1, -1, f_out, nullptr,
+                                                                 nullptr, c.err, it);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
-int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, const double* fac, int ik1, int ik2,
-               int idr, bool emit_keys, cudaStream_t s) {
+// F is [3][M] (f4 = false) or interleaved float4 [M] (f4 = true).
+int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
+               int ik2, int idr, bool emit_keys, cudaStream_t s) {
   if (emit_keys) FPM_CUDA_TRY(cudaMemsetAsync(c.tile_count, 0, sizeof(uint32_t) * c.ntiles, s));
-  k_readout<true><<<grid_of(c.N, 256), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr, nullptr,
-                                                    emit_keys ? c.keys : nullptr, c.tile_count, c.err);
+  const int it = readout_iters(c.N);
+  uint32_t* keys = emit_keys ? c.keys : nullptr;
+  if (f4)
+    k_readout<true, true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr,
+                                                                 nullptr, keys, c.tile_count, c.err, it);
+  else
+    k_readout<true, false><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr,
+                                                                  nullptr, keys, c.tile_count, c.err, it);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }

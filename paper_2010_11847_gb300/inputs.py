@@ -47,6 +47,8 @@ class Workload:
 SMALL = Workload("pm_32p_32m_100mpc_5step", 32, 32, 100.0, 5)
 MEDIUM = Workload("pm_128p_256m_400mpc_10step", 128, 256, 400.0, 10)
 LARGE = Workload("pm_512p_512m_1000mpc_40step", 512, 512, 1000.0, 40)
+# 1/8 of LARGE at the same cell size and particle density (profiling case)
+LARGE_EIGHTH = Workload("pm_256p_256m_500mpc_40step", 256, 256, 500.0, 40)
 DIFFERENTIABLE = Workload("pm_128p_128m_400mpc_5step_adjoint", 128, 128, 400.0, 5)
 
 
