@@ -139,6 +139,23 @@ int fpm_kdk(fpm_plan* plan, float* dx, float* p, const double* a, int nsteps,
 int fpm_power(fpm_plan* plan, const float* a, const float* b, double* pk,
               double* kmean, double* nmodes, void* stream);
 
+/* CIC paint that allocates nothing (the paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc -- code running while a
+ * stream is captured into a CUDA graph, loops that cannot afford
+ * cudaMalloc's implicit device synchronisation, hosts that own all device
+ * memory).  Same result as fpm_paint without a plan: rho (float[nc^3],
+ * mean 1) of np^3 particles at q + dx (dx: float[3][np^3]); both caller
+ * device buffers.  Scratch is one fixed file-scope device array of about
+ * 2.9 MB that every GPU loading the library keeps until exit; sizes above
+ * its maximum -- np or nc larger than 64 -- are rejected with FPM_EINVAL,
+ * as are unsupported sizes.  The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  All calls share the array: calls whose execution
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Device-side error flags are not reported by
+ * this variant.  Asynchronous on `stream`. */
+int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream);
+
 /* Kernel classes of the per-class timing below. */
 #define FPM_K_KDK 0       /* CIC readout fused with kick, drift and new keys */
 #define FPM_K_KEYS 1      /* cell keys + tile histogram (first paint)        */

@@ -23,7 +23,7 @@ FPM_OK, FPM_EINVAL, FPM_ENOMEM, FPM_ECUDA, FPM_ETIMEOUT, FPM_EDEVICE, FPM_ENOTIM
 EXPORTS = [
     "fpm_plan_create", "fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_growth", "fpm_linear_field",
     "fpm_lpt", "fpm_paint", "fpm_force", "fpm_readout", "fpm_kdk", "fpm_power", "fpm_status", "fpm_strerror",
-    "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count",
+    "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
 ]
 FPM_K_COUNT = 15
 
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_kernel_class_name.restype = ctypes.c_char_p
     L.fpm_launch_count.argtypes = []
     L.fpm_launch_count.restype = i64
+    L.fpm_paint_noalloc.argtypes = [i, i, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_strerror", "fpm_kernel_class_name",
                         "fpm_launch_count"):
@@ -218,6 +219,14 @@ class Plan:
         dx, p = self.lpt(lin_k, float(a[0]), order, stream=stream)
         self.kdk(dx, p, a, ckpt=ckpt, stream=stream)
         return dx, p, lin_k
+
+
+def paint_noalloc(np_: int, nc: int, dx, rho, stream=None):
+    """fpm_paint_noalloc: the CIC paint for callers that cannot allocate
+    device memory (no plan; fixed scratch inside the library, np, nc <= 64).
+    The caller passes both device buffers; nothing is allocated here."""
+    _check("fpm_paint_noalloc", lib().fpm_paint_noalloc(int(np_), int(nc), _ptr(dx), _ptr(rho), _stream(stream)))
+    return rho
 
 
 def launch_count() -> int:
