@@ -25,6 +25,7 @@ Conventions (the paper is silent on these; each is a stated reading):
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -99,6 +100,14 @@ def _growth_raw(a_targets, omega_m):
     return y
 
 
+@functools.lru_cache(maxsize=256)
+def _growth_raw_cached(a_targets, omega_m):
+    """_growth_raw memoised on its (hashable) arguments; same arithmetic."""
+    out = _growth_raw(np.array(a_targets), omega_m)
+    out.setflags(write=False)
+    return out
+
+
 def growth(a, omega_m):
     """Normalised growth quantities at scale factors a.
 
@@ -107,7 +116,7 @@ def growth(a, omega_m):
     D1, D2, f1 = dlnD1/dlna, f2 = dlnD2/dlna, dD1da = dD1/da, E.
     """
     a = np.atleast_1d(np.asarray(a, dtype=np.float64))
-    raw = _growth_raw(np.concatenate([a, [1.0]]), omega_m)
+    raw = _growth_raw_cached(tuple(np.concatenate([a, [1.0]]).tolist()), float(omega_m))
     norm = raw[0, -1]
     d1, d1p, d2, d2p = raw[:, :-1]
     return dict(
@@ -342,11 +351,17 @@ def lattice(np_, nc):
     return np.stack([ix * r, iy * r, iz * r])
 
 
+POSITIONS_FP32 = True    # positions are float32 displacements; False: keep FP64 (derivative pins)
+
+
 def cic_cells(dx, np_, nc):
     """Base cell and fractional offset of each particle from its float32
     displacement dx (3, N): cell = wrap(q + floor(dx)), t = dx - floor(dx).
     floor() of the float32 value is exact, so the cell is exact."""
-    dx64 = np.asarray(dx, dtype=np.float32).astype(np.float64)
+    if POSITIONS_FP32:
+        dx64 = np.asarray(dx, dtype=np.float32).astype(np.float64)
+    else:
+        dx64 = np.asarray(dx, dtype=np.float64)
     fl = np.floor(dx64)
     cell = (lattice(np_, nc) + fl.astype(np.int64)) % nc
     t = dx64 - fl
@@ -544,3 +559,179 @@ def simulate(white, nc, box, cosmo, stages, order=2, record=None):
     rho = paint(dx.astype(np.float32), np_, nc)
     k, pk, _ = power_spectrum(rho - 1.0, box)
     return dict(dx=dx, p=p, rho=rho, k=k, pk=pk, lin_k=lin_k, dx0=dx0, p0=p0)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (reverse mode) of the forward model: the differentiability the
+# paper names as the method's main advantage (Sec. 8), through the chi^2 of
+# Eq. 12's likelihood term.  Every function returns the transpose (or the
+# transposed Jacobian) of the forward function of the same name applied to a
+# cotangent; cotangents of real fields are real fields of the same shape.
+# ---------------------------------------------------------------------------
+def chi2(rho, delta_target, sigma=1.0):
+    """chi^2 = sum (delta - delta_t)^2 / sigma^2 with delta = rho - 1, and its
+    gradient with respect to rho."""
+    r = (np.asarray(rho, dtype=np.float64) - 1.0 - delta_target) / sigma
+    return float((r * r).sum()), 2.0 * r / sigma
+
+
+def _corner_grad(t, b, d):
+    """d/dt_d of the CIC corner weight prod_e (b_e ? t_e : 1 - t_e)."""
+    w = np.ones(t.shape[1])
+    for e in range(3):
+        if e == d:
+            w = w * (1.0 if b[e] else -1.0)
+        else:
+            w = w * (t[e] if b[e] else (1.0 - t[e]))
+    return w
+
+
+def _gather_grad(field, cell, t):
+    """sum_c dW(x_i - c)/dx_d field_c for d = 0..2 (right derivative at
+    integer positions, matching the floor-based cell)."""
+    nc = field.shape[-1]
+    flat_field = field.reshape(-1)
+    out = np.zeros((3, cell.shape[1]))
+    for b in _corners():
+        c = [(cell[e] + b[e]) % nc for e in range(3)]
+        vals = flat_field[(c[0] * nc + c[1]) * nc + c[2]]
+        for d in range(3):
+            out[d] += vals * _corner_grad(t, b, d)
+    return out
+
+
+def paint_adj(g_rho, dx, np_, nc):
+    """Transposed Jacobian of paint: g_dx_i = m sum_c grad W(x_i - c) g_rho_c."""
+    cell, t = cic_cells(dx, np_, nc)
+    m = (nc / np_) ** 3
+    return m * _gather_grad(np.asarray(g_rho, dtype=np.float64), cell, t)
+
+
+def readout_adj(F, dx, g_f, np_, nc):
+    """Transposed Jacobian of readout f = R(x; F): the mesh cotangent
+    g_F[d] = sum_i W(x_i - c) g_f[d][i] (a paint of g_f) and the position
+    cotangent g_dx_i = sum_d g_f[d][i] sum_c grad W(x_i - c) F[d]_c."""
+    cell, t = cic_cells(dx, np_, nc)
+    g_F = np.stack([paint_cells(cell, t, np.asarray(g_f[d], dtype=np.float64), nc) for d in range(3)])
+    g_dx = np.zeros((3, cell.shape[1]))
+    for d in range(3):
+        g_dx += np.asarray(g_f[d])[None, :] * _gather_grad(np.asarray(F[d], dtype=np.float64), cell, t)
+    return g_F, g_dx
+
+
+def force_adj(g_F, omega_m):
+    """Transpose of delta -> F (Eqs. 3-5): each F_d is a convolution with a
+    real odd kernel, so its transpose is its negative:
+    g_delta = -sum_d IFFT(i g_d 1.5 Om FFT(g_F_d) / |w|^2)."""
+    n = g_F.shape[-1]
+    g = _gradient_kernels(n)
+    k2 = _laplacian_naive(n)
+    k2[0, 0, 0] = 1.0
+    acc = 0.0
+    for d in range(3):
+        acc = acc + 1j * g[d] * _rfftn(np.asarray(g_F[d], dtype=np.float64))
+    acc = 1.5 * omega_m * acc / k2
+    acc[0, 0, 0] = 0.0
+    return -_irfftn(acc, n)
+
+
+def particle_force_adj(dx, g_f, np_, nc, omega_m):
+    """Transposed Jacobian of dx -> particle_force(dx) applied to g_f."""
+    F = force(paint(dx, np_, nc), omega_m)
+    g_F, g_dx = readout_adj(F, dx, g_f, np_, nc)
+    g_rho = force_adj(g_F, omega_m)
+    return g_dx + paint_adj(g_rho, dx, np_, nc)
+
+
+def kdk_adj(xs, stages, g_dx, g_p, np_, nc, omega_m):
+    """Reverse of ``kdk`` given the positions x_k at every stage (xs[k],
+    float32-rounded as the forward used them) and the cotangents of the final
+    (dx, p).  Undoes, for k = n-1..0: the closing kick at x_{k+1}, the drift,
+    the opening kick at x_k.  Returns the cotangents of the initial (dx, p)."""
+    kick1, drift, kick2 = fastpm_factors(stages, omega_m)
+    gx = np.array(g_dx, dtype=np.float64)
+    gp = np.array(g_p, dtype=np.float64)
+    n = len(stages) - 1
+    for k in range(n - 1, -1, -1):
+        gx = gx + particle_force_adj(xs[k + 1], kick2[k] * gp, np_, nc, omega_m)
+        gp = gp + drift[k] * gx
+        gx = gx + particle_force_adj(xs[k], kick1[k] * gp, np_, nc, omega_m)
+    return gx, gp
+
+
+def lpt_adj(lin_k, nc, a0, cosmo, g_dx, g_p, order=2):
+    """Reverse of ``lpt``: returns G = FFT(dL/d delta_L), the unnormalised DFT
+    of the cotangent of the real linear field delta_L = IFFT(lin_k)
+    (rfftn layout).  Psi1_d = B_d delta_L and Psi2_d = -B_d S with B_d the
+    convolution of transfer i g_d/|w|^2 (real odd, B_d^T = -B_d), and
+    phi_ij = H_ij delta_L with transfer g_i g_j/|w|^2 (real even, H^T = H)."""
+    np_ = lin_k.shape[0]
+    gr = growth([a0], cosmo["omega_m"])
+    D1, D2, f1, f2, E = (float(gr[k][0]) for k in ("D1", "D2", "f1", "f2", "E"))
+    r = nc / np_
+    shape = (3, np_, np_, np_)
+    gdx = np.asarray(g_dx, dtype=np.float64).reshape(shape)
+    gp = np.asarray(g_p, dtype=np.float64).reshape(shape)
+    pf = a0 * a0 * E
+    g_psi1 = r * (D1 * gdx + pf * f1 * D1 * gp)
+    g_psi2 = r * (D2 * gdx + pf * f2 * D2 * gp)
+    g = _gradient_kernels(np_)
+    k2 = _laplacian_naive(np_)
+    k2[0, 0, 0] = 1.0
+    inv_k2 = 1.0 / k2
+    inv_k2[0, 0, 0] = 0.0
+    # B_d^T g = -IFFT(i g_d FFT(g) / |w|^2)
+    G = 0.0
+    for d in range(3):
+        G = G - 1j * g[d] * _rfftn(g_psi1[d]) * inv_k2
+    if order == 2:
+        # dL/dS = sum_d (-B_d)^T g_psi2_d = sum_d B_d g_psi2_d
+        gS = _irfftn(sum(1j * g[d] * _rfftn(g_psi2[d]) for d in range(3)) * inv_k2, np_)
+        phi = {}
+        for i in range(3):
+            for j in range(i, 3):
+                phi[(i, j)] = _irfftn(g[i] * g[j] * lin_k * inv_k2, np_)
+        # S = sum_{i<j} (phi_ii phi_jj - phi_ij^2)
+        g_phi = {
+            (0, 0): gS * (phi[(1, 1)] + phi[(2, 2)]),
+            (1, 1): gS * (phi[(0, 0)] + phi[(2, 2)]),
+            (2, 2): gS * (phi[(0, 0)] + phi[(1, 1)]),
+            (0, 1): -2.0 * gS * phi[(0, 1)],
+            (0, 2): -2.0 * gS * phi[(0, 2)],
+            (1, 2): -2.0 * gS * phi[(1, 2)],
+        }
+        for (i, j), v in g_phi.items():
+            G = G + g[i] * g[j] * inv_k2 * _rfftn(v)
+    return G
+
+
+def linear_field_adj(G, box, cosmo):
+    """Reverse of ``linear_field`` given G = FFT(dL/d delta_L): the map
+    w -> delta_L is a convolution with the real even transfer
+    s(k) = sqrt(P(k) N^3 / V), so g_w = IFFT(s G)."""
+    n = G.shape[0]
+    nx, ny, nz = half_spectrum_wavenumbers(n)
+    kmag = 2.0 * math.pi / box * np.sqrt((nx * nx + ny * ny + nz * nz).astype(np.float64))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        pk = linear_pk(kmag, cosmo)
+    s = np.sqrt(pk * n ** 3 / box ** 3)
+    s[0, 0, 0] = 0.0
+    return _irfftn(s * G, n)
+
+
+def chi2_and_grad(white, delta_target, nc, box, cosmo, stages, sigma=1.0, order=2):
+    """chi^2 of the final CIC density against delta_target and its gradient
+    with respect to the white noise (the reverse of ``simulate``)."""
+    np_ = white.shape[0]
+    xs = []
+    lin_k = linear_field(white, box, cosmo)
+    dx0, p0 = lpt(lin_k, nc, stages[0], cosmo, order=order)
+    dx, p = kdk(dx0, p0, stages, np_, nc, cosmo["omega_m"], record=xs, round_to_float32=POSITIONS_FP32)
+    ptype = np.float32 if POSITIONS_FP32 else np.float64
+    xs = [x.astype(ptype) for x, _ in xs] + [dx.astype(ptype)]
+    rho = paint(xs[-1], np_, nc)
+    loss, g_rho = chi2(rho, delta_target, sigma)
+    g_dx = paint_adj(g_rho, xs[-1], np_, nc)
+    g_dx0, g_p0 = kdk_adj(xs, stages, g_dx, np.zeros_like(g_dx), np_, nc, cosmo["omega_m"])
+    G = lpt_adj(lin_k, nc, stages[0], cosmo, g_dx0, g_p0, order=order)
+    return loss, linear_field_adj(G, box, cosmo)
