@@ -139,6 +139,67 @@ int fpm_kdk(fpm_plan* plan, float* dx, float* p, const double* a, int nsteps,
 int fpm_power(fpm_plan* plan, const float* a, const float* b, double* pk,
               double* kmean, double* nmodes, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Adjoints (reverse mode).  The paper's reconstruction (Sec. 7, Eq. 12)
+ * needs the gradient of a chi^2 between the final density and data with
+ * respect to the initial conditions; these entry points are the transposed
+ * Jacobians of the forward steps, applied to cotangents of the same
+ * layouts.  Adjoint entry points that transform meshes need power-of-two
+ * np and nc (else FPM_ENOTIMPL).  The first adjoint call on a plan
+ * allocates the adjoint scratch (cudaMalloc; make it before any stream
+ * capture).  All return-by-argument buffers are overwritten unless stated.
+ * ------------------------------------------------------------------- */
+
+/* chi^2 of Eq. 12's likelihood term: loss = sum_c (rho_c - 1 - t_c)^2 /
+ * sigma^2 with t = target_delta (float[nc^3]), accumulated in FP64 in a
+ * fixed order; g_rho (nullable, float[nc^3]) = 2 (rho - 1 - t) / sigma^2.
+ * loss (nullable) is a HOST double; when given, `stream` is synchronised. */
+int fpm_chi2(fpm_plan* plan, const float* rho, const float* target_delta, double sigma,
+             float* g_rho, double* loss, void* stream);
+
+/* Transposed Jacobian of fpm_paint with respect to dx:
+ * g_dx[d][i] = m sum_c dW(q_i + dx_i - c)/dx_d g_rho[c]  (m = (nc/np)^3;
+ * right derivative where a particle sits exactly on a cell boundary). */
+int fpm_paint_adj(fpm_plan* plan, const float* dx, const float* g_rho, float* g_dx,
+                  void* stream);
+
+/* Transposed Jacobian of fpm_readout(F, dx) applied to g_f (float[3][np^3]):
+ * g_F[d][c] = sum_i W(q_i + dx_i - c) g_f[d][i] (float[3][nc^3], a
+ * deterministic fixed-point scatter) and
+ * g_dx[e][i] = sum_d g_f[d][i] sum_c dW/dx_e F[d][c]. */
+int fpm_readout_adj(fpm_plan* plan, const float* F, const float* dx, const float* g_f,
+                    float* g_F, float* g_dx, void* stream);
+
+/* Transpose of fpm_force's linear map rho -> F: each F_d is a convolution
+ * with a real odd kernel, so g_rho = -sum_d IDFT(i g_d 1.5 omega_m
+ * DFT(g_F_d) / |w|^2).  g_F: float[3][nc^3]; g_rho: float[nc^3]. */
+int fpm_force_adj(fpm_plan* plan, const float* g_F, float* g_rho, void* stream);
+
+/* Reverse of fpm_kdk over the same HOST scale factors a[0..nsteps], given
+ * its checkpoints ckpt (float[nsteps+1][3][np^3], dx at every a_k).  On
+ * entry g_dx holds the cotangent of the final dx and g_p_in (nullable:
+ * zero, e.g. a loss on the density alone) that of the final p; on return
+ * g_dx and g_p (required, may equal g_p_in) hold the cotangents of the
+ * initial dx and p.  Each reverse step recomputes the force at the
+ * checkpoint, then applies the drift transpose and the transposed force
+ * Jacobian (readout, force and paint transposes). */
+int fpm_kdk_adj(fpm_plan* plan, const float* ckpt, const double* a, int nsteps, float* g_dx,
+                const float* g_p_in, float* g_p, void* stream);
+
+/* Reverse of fpm_lpt: from the cotangents of dx and p (float[3][np^3])
+ * returns g_lin_k = DFT(dL/d delta_L), the unnormalised DFT of the
+ * cotangent of the real linear field delta_L = IDFT(lin_k), in the lin_k
+ * layout.  Uses Psi1_d = B_d delta_L, Psi2_d = -B_d S with B_d the real odd
+ * convolution of transfer i g_d / |w|^2 (B_d^T = -B_d) and the chain rule
+ * through S = sum_{i<j} (phi_ii phi_jj - phi_ij^2). */
+int fpm_lpt_adj(fpm_plan* plan, const void* lin_k, double a0, int order, const float* g_dx,
+                const float* g_p, void* g_lin_k, void* stream);
+
+/* Reverse of fpm_linear_field: the map white -> delta_L is a convolution
+ * with the real even transfer s(k) = sqrt(P(k) np^3 / box^3), so
+ * g_white = IDFT(s g_lin_k) (float[np^3]). */
+int fpm_linear_field_adj(fpm_plan* plan, const void* g_lin_k, float* g_white, void* stream);
+
 /* CIC paint that allocates nothing (the paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc -- code running while a
  * stream is captured into a CUDA graph, loops that cannot afford

@@ -24,6 +24,8 @@ EXPORTS = [
     "fpm_plan_create", "fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_growth", "fpm_linear_field",
     "fpm_lpt", "fpm_paint", "fpm_force", "fpm_readout", "fpm_kdk", "fpm_power", "fpm_status", "fpm_strerror",
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
+    "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
+    "fpm_linear_field_adj",
 ]
 FPM_K_COUNT = 15
 
@@ -71,6 +73,13 @@ def lib() -> ctypes.CDLL:
     L.fpm_launch_count.argtypes = []
     L.fpm_launch_count.restype = i64
     L.fpm_paint_noalloc.argtypes = [i, i, vp, vp, vp]
+    L.fpm_chi2.argtypes = [vp, vp, vp, d, vp, vp, vp]
+    L.fpm_paint_adj.argtypes = [vp, vp, vp, vp, vp]
+    L.fpm_readout_adj.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.fpm_force_adj.argtypes = [vp, vp, vp, vp]
+    L.fpm_kdk_adj.argtypes = [vp, vp, vp, i, vp, vp, vp, vp]
+    L.fpm_lpt_adj.argtypes = [vp, vp, d, i, vp, vp, vp, vp]
+    L.fpm_linear_field_adj.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_strerror", "fpm_kernel_class_name",
                         "fpm_launch_count"):
@@ -212,6 +221,55 @@ class Plan:
                                                           _stream(stream)))
         return {lib().fpm_kernel_class_name(k).decode(): (float(ms[k]), int(cnt[k]))
                 for k in range(FPM_K_COUNT) if cnt[k]}
+
+    # adjoints -----------------------------------------------------------------
+    def chi2(self, rho, target_delta, sigma=1.0, g_rho=None, want_grad=True, stream=None):
+        """(loss, g_rho) of sum (rho - 1 - target)^2 / sigma^2."""
+        if want_grad and g_rho is None:
+            g_rho = self._empty(self.nc, self.nc, self.nc)
+        loss = ctypes.c_double()
+        _check("fpm_chi2", lib().fpm_chi2(self._h, _ptr(rho), _ptr(target_delta), float(sigma),
+                                          _ptr(g_rho) if want_grad else None, ctypes.byref(loss), _stream(stream)))
+        return loss.value, g_rho
+
+    def paint_adj(self, dx, g_rho, g_dx=None, stream=None):
+        g_dx = g_dx if g_dx is not None else self._empty(3, self.N)
+        _check("fpm_paint_adj", lib().fpm_paint_adj(self._h, _ptr(dx), _ptr(g_rho), _ptr(g_dx), _stream(stream)))
+        return g_dx
+
+    def readout_adj(self, F, dx, g_f, stream=None):
+        g_F = self._empty(3, self.nc, self.nc, self.nc)
+        g_dx = self._empty(3, self.N)
+        _check("fpm_readout_adj", lib().fpm_readout_adj(self._h, _ptr(F), _ptr(dx), _ptr(g_f), _ptr(g_F),
+                                                        _ptr(g_dx), _stream(stream)))
+        return g_F, g_dx
+
+    def force_adj(self, g_F, g_rho=None, stream=None):
+        g_rho = g_rho if g_rho is not None else self._empty(self.nc, self.nc, self.nc)
+        _check("fpm_force_adj", lib().fpm_force_adj(self._h, _ptr(g_F), _ptr(g_rho), _stream(stream)))
+        return g_rho
+
+    def kdk_adj(self, ckpt, a, g_dx, g_p_in=None, g_p=None, stream=None):
+        """Cotangents of the initial (dx, p) from those of the final ones
+        (g_p_in None: the loss does not depend on the final momenta)."""
+        a = _host_f64(a).ravel()
+        g_p = g_p if g_p is not None else self._empty(3, self.N)
+        _check("fpm_kdk_adj", lib().fpm_kdk_adj(self._h, _ptr(ckpt), a.ctypes.data, a.size - 1, _ptr(g_dx),
+                                                _ptr(g_p_in), _ptr(g_p), _stream(stream)))
+        return g_dx, g_p
+
+    def lpt_adj(self, lin_k, a0, g_dx, g_p, order=2, g_lin_k=None, stream=None):
+        import torch
+        g_lin_k = g_lin_k if g_lin_k is not None else self._empty(self.spectrum_shape(), dtype=torch.complex64)
+        _check("fpm_lpt_adj", lib().fpm_lpt_adj(self._h, _ptr(lin_k), float(a0), int(order), _ptr(g_dx), _ptr(g_p),
+                                                _ptr(g_lin_k), _stream(stream)))
+        return g_lin_k
+
+    def linear_field_adj(self, g_lin_k, g_white=None, stream=None):
+        g_white = g_white if g_white is not None else self._empty(self.np, self.np, self.np)
+        _check("fpm_linear_field_adj", lib().fpm_linear_field_adj(self._h, _ptr(g_lin_k), _ptr(g_white),
+                                                                  _stream(stream)))
+        return g_white
 
     # a whole forward model (Algorithm 4 + KDK) ------------------------------
     def simulate(self, white, a, order: int = 2, ckpt=None, stream=None):

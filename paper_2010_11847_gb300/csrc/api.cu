@@ -57,6 +57,15 @@ struct fpm_plan {
   int* d_err = nullptr;
   int64_t scratch_bytes = 0;
   Profiler prof;
+  // adjoint scratch, allocated by the first adjoint call
+  float2* aspec = nullptr;     // 9 half spectra of the lattice
+  float* adj6 = nullptr;       // 6 lattice fields (cotangents of Psi1, Psi2)
+  float* gS = nullptr;         // lattice field (cotangent of the 2LPT source)
+  float* gF = nullptr;         // 3 meshes (cotangent of the force meshes)
+  float* vbuf = nullptr;       // [3][N] kick-weighted momentum cotangent
+  unsigned* vmax = nullptr;    // max |v| bits for the signed fixed point
+  double* partial = nullptr;   // chi^2 block partials
+  double* d_loss = nullptr;
 };
 
 namespace {
@@ -100,6 +109,14 @@ void free_plan(fpm_plan* p) {
   cudaFree(p->d_fac);
   cudaFree(p->d_bins);
   cudaFree(p->d_err);
+  cudaFree(p->aspec);
+  cudaFree(p->adj6);
+  cudaFree(p->gS);
+  cudaFree(p->gF);
+  cudaFree(p->vbuf);
+  cudaFree(p->vmax);
+  cudaFree(p->partial);
+  cudaFree(p->d_loss);
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   if (p->tc.tw) fft_tables_destroy(&p->tc);
   if (!p->share_tables && p->tp.tw) fft_tables_destroy(&p->tp);
@@ -450,7 +467,193 @@ const char* fpm_kernel_class_name(int cls) {
 
 int64_t fpm_launch_count(void) { return (int64_t)g_launches.load(); }
 
-int fpm_status(fpm_plan* p, void* stream) {
+// ---------------------------------------------------------------- adjoints
+static constexpr int CHI_PARTIALS = 1024;
+
+static int ensure_adjoint(fpm_plan* p) {
+  if (p->gF) return FPM_OK;
+  if (!fft_has_interleaved(p->np) || !fft_has_interleaved(p->nc)) return FPM_ENOTIMPL;
+  const size_t sp = spec_elems(p->np);
+  int rc;
+  if ((rc = dalloc(p, &p->aspec, 9 * sp)) || (rc = dalloc(p, &p->adj6, 6 * p->N)) || (rc = dalloc(p, &p->gS, p->N)) ||
+      (rc = dalloc(p, &p->vbuf, 3 * p->N)) || (rc = dalloc(p, &p->vmax, 1)) ||
+      (rc = dalloc(p, &p->partial, CHI_PARTIALS)) || (rc = dalloc(p, &p->d_loss, 1)) ||
+      (rc = dalloc(p, &p->gF, 3 * p->M)))
+    return rc;
+  return FPM_OK;
+}
+
+// g_rho = -sum_d A_d g_F_d (A_d^T = -A_d for the real odd force kernels).
+static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream_t s) {
+  const FftTables& t = p->tc;
+  FPM_TRY(timed(p, FPM_K_FFT_ZF, 1, s, [&] { return fft_zfwd(t, gF, p->spec, 3, p->M, p->specmax, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_YF, 1, s, [&] { return fft_y(t, p->spec, 3, p->specmax, false, s); }));
+  XSource src[3];
+  for (int d = 0; d < 3; ++d) src[d] = XSource{p->spec + d * p->specmax, SK_FORCE_NEG, d, 0, 0};
+  FPM_TRY(timed(p, FPM_K_FFT_X, 1, s, [&] {
+    return fft_xcombine(t, src, 3, (float)(1.0 / (double)p->M), p->cosmo.omega_m, nullptr, nullptr, 0.f, 0.f,
+                        p->spec, 1, s);
+  }));
+  FPM_TRY(timed(p, FPM_K_FFT_YI, 1, s, [&] { return fft_y(t, p->spec, 1, 0, true, s); }));
+  FPM_TRY(timed(p, FPM_K_FFT_ZI, 1, s, [&] { return fft_zinv(t, p->spec, g_rho, 1, 0, 0, s); }));
+  return FPM_OK;
+}
+
+// gx += J_f(x)^T v at the positions x whose paint (buckets) and force
+// meshes (p->F, interleaved when p->f4) are current; uses p->rho as scratch.
+static int force_jt_impl(fpm_plan* p, const float* x, const float* v, float* gx, cudaStream_t s) {
+  FPM_TRY(timed(p, FPM_K_PAINT, 7, s, [&] { return launch_paint_vec(p->pc, x, v, p->vmax, p->gF, s); }));
+  FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
+  return timed(p, FPM_K_READOUT, 1, s,
+               [&] { return launch_gather_adj(p->pc, x, p->rho, p->F, p->f4, v, gx, true, s); });
+}
+
+extern "C" {
+
+int fpm_chi2(fpm_plan* p, const float* rho, const float* target, double sigma, float* g_rho, double* loss,
+             void* stream) {
+  if (!p || !rho || !target || !(sigma > 0)) return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  FPM_TRY(launch_chi2(rho, target, p->M, (float)sigma, g_rho, p->partial, CHI_PARTIALS, p->d_loss, s));
+  g_launches += 2;
+  if (loss) {
+    FPM_CUDA_TRY(cudaMemcpyAsync(loss, p->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return FPM_OK;
+}
+
+int fpm_paint_adj(fpm_plan* p, const float* dx, const float* g_rho, float* g_dx, void* stream) {
+  if (!p || !dx || !g_rho || !g_dx) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  return timed(p, FPM_K_READOUT, 1, s,
+               [&] { return launch_gather_adj(p->pc, dx, g_rho, nullptr, false, nullptr, g_dx, false, s); });
+}
+
+int fpm_readout_adj(fpm_plan* p, const float* F, const float* dx, const float* g_f, float* g_F, float* g_dx,
+                    void* stream) {
+  if (!p || !F || !dx || !g_f || !g_F || !g_dx) return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  PaintCtx c = p->pc;
+  FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, dx, s); }));
+  FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
+  FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, 7, s, [&] { return launch_paint_vec(c, dx, g_f, p->vmax, g_F, s); }));
+  return timed(p, FPM_K_READOUT, 1, s,
+               [&] { return launch_gather_adj(c, dx, nullptr, F, false, g_f, g_dx, false, s); });
+}
+
+int fpm_force_adj(fpm_plan* p, const float* g_F, float* g_rho, void* stream) {
+  if (!p || !g_F || !g_rho) return FPM_EINVAL;
+  if (!fft_has_interleaved(p->nc)) return FPM_ENOTIMPL;
+  return force_adj_impl(p, g_F, g_rho, S(stream));
+}
+
+int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const double* a, int nsteps, float* g_dx, const float* g_p_in,
+                float* g_p, void* stream) {
+  if (!p || !ckpt || !a || !g_dx || !g_p || nsteps < 1 || nsteps > MAX_STEPS) return FPM_EINVAL;
+  for (int k = 0; k <= nsteps; ++k)
+    if (!(a[k] > 1e-5 && a[k] <= 10.0) || (k > 0 && !(a[k] > a[k - 1]))) return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  std::vector<double> pts(a, a + nsteps + 1);
+  for (int k = 0; k < nsteps; ++k) pts.push_back(sqrt(a[k] * a[k + 1]));
+  FPM_TRY(stage_points(p, pts.data(), (int)pts.size(), s));
+  FPM_TRY(timed(p, FPM_K_COEF, 3, s, [&] {
+    return launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s);
+  }));
+  const size_t N3 = 3 * p->N;
+  float* gp = g_p;
+  if (g_p_in) {
+    if (g_p_in != g_p)
+      FPM_CUDA_TRY(cudaMemcpyAsync(gp, g_p_in, N3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  } else {     // the loss does not depend on the final momenta: start from zero
+    FPM_CUDA_TRY(cudaMemsetAsync(gp, 0, N3 * sizeof(float), s));
+  }
+  auto recompute = [&](const float* x) -> int {
+    FPM_TRY(paint_impl(p, x, p->rho, nullptr, nullptr, s));
+    return force_impl(p, p->rho, p->F, s, p->f4);
+  };
+  if (g_p_in) {   // closing half kick at a_n: gx += J^T(x_n) (K gp)
+    const float* xn = ckpt + (size_t)nsteps * N3;
+    FPM_TRY(recompute(xn));
+    FPM_TRY(launch_scale_copy(gp, p->vbuf, N3, p->d_fac, 3 * (nsteps - 1) + 2, s));
+    FPM_TRY(force_jt_impl(p, xn, p->vbuf, g_dx, s));
+  }
+  for (int k = nsteps - 1; k >= 0; --k) {
+    const float* xk = ckpt + (size_t)k * N3;
+    // drift transpose, then the merged kick at x_k (opening kick of step k
+    // and closing kick of step k-1 share the force at a_k)
+    FPM_TRY(launch_adj_drift_kick(g_dx, gp, p->vbuf, N3, p->d_fac, 3 * k + 1, 3 * k + 0,
+                                  k > 0 ? 3 * (k - 1) + 2 : -1, s));
+    FPM_TRY(recompute(xk));
+    FPM_TRY(force_jt_impl(p, xk, p->vbuf, g_dx, s));
+  }
+  g_launches += 1 + 2 * nsteps;
+  return FPM_OK;
+}
+
+int fpm_lpt_adj(fpm_plan* p, const void* lin_k, double a0, int order, const float* g_dx, const float* g_p,
+                void* g_lin_k, void* stream) {
+  if (!p || !lin_k || !g_dx || !g_p || !g_lin_k || (order != 1 && order != 2) || !(a0 > 1e-5 && a0 <= 10.0))
+    return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  const FftTables& t = p->tp;
+  const size_t sp = spec_elems(p->np), N = p->N;
+  const float2* lk = reinterpret_cast<const float2*>(lin_k);
+  float2* out = reinterpret_cast<float2*>(g_lin_k);
+  const float inv_n3 = (float)(1.0 / (double)N);
+  FPM_TRY(stage_points(p, &a0, 1, s));
+  FPM_TRY(timed(p, FPM_K_COEF, 2, s, [&] { return launch_growth(p->d_pts, 1, p->cosmo.omega_m, p->d_raw, p->d_gr, s); }));
+  return timed(p, FPM_K_IC, order == 2 ? 17 : 4, s, [&] {
+    FPM_TRY(launch_lpt_gpsi(g_dx, g_p, N, p->d_gr, (float)a0, (float)(p->nc / p->np), p->adj6, s));
+    XSource src[9];
+    int ns = 0;
+    if (order == 2) {
+      // phi_ij of the forward model, then g_S = sum_d B_d g_Psi2_d
+      FPM_TRY(fft_xlpt_hessian(t, lk, p->spec, p->specmax, inv_n3, s));
+      FPM_TRY(fft_y(t, p->spec, 6, p->specmax, true, s));
+      FPM_TRY(fft_zinv(t, p->spec, p->real6, 6, p->specmax, N, s));
+      FPM_TRY(fft_zfwd(t, p->adj6 + 3 * N, p->aspec, 3, N, sp, s));
+      FPM_TRY(fft_y(t, p->aspec, 3, sp, false, s));
+      for (int d = 0; d < 3; ++d) src[d] = XSource{p->aspec + d * sp, SK_B, d, 0, 0};
+      FPM_TRY(fft_xcombine(t, src, 3, inv_n3, 0.0, nullptr, nullptr, 0.f, 0.f, p->aspec, 1, s));
+      FPM_TRY(fft_y(t, p->aspec, 1, 0, true, s));
+      FPM_TRY(fft_zinv(t, p->aspec, p->gS, 1, 0, 0, s));
+      FPM_TRY(launch_lpt_gphi(p->gS, p->real6, N, s));
+      FPM_TRY(fft_zfwd(t, p->real6, p->aspec + 3 * sp, 6, N, sp, s));
+      FPM_TRY(fft_y(t, p->aspec + 3 * sp, 6, sp, false, s));
+      const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+      for (int q = 0; q < 6; ++q) src[ns++] = XSource{p->aspec + (3 + q) * sp, SK_H, pi[q], pj[q], 0};
+    }
+    FPM_TRY(fft_zfwd(t, p->adj6, p->aspec, 3, N, sp, s));
+    FPM_TRY(fft_y(t, p->aspec, 3, sp, false, s));
+    for (int d = 0; d < 3; ++d) src[ns++] = XSource{p->aspec + d * sp, SK_BCONJ, d, 0, 0};
+    return fft_xcombine(t, src, ns, 1.f, 0.0, nullptr, nullptr, 0.f, 0.f, out, 0, s);
+  });
+}
+
+int fpm_linear_field_adj(fpm_plan* p, const void* g_lin_k, float* g_white, void* stream) {
+  if (!p || !g_lin_k || !g_white) return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  const FftTables& t = p->tp;
+  const double n3v = (double)p->N / (p->box * p->box * p->box);
+  XSource src{reinterpret_cast<const float2*>(g_lin_k), SK_LINEAR, 0, 0, 1};
+  return timed(p, FPM_K_IC, 3, s, [&] {
+    FPM_TRY(fft_xcombine(t, &src, 1, (float)(1.0 / (double)p->N), 0.0, &p->eh, p->d_amp,
+                         (float)(6.283185307179586 / p->box), (float)n3v, p->aspec, 1, s));
+    FPM_TRY(fft_y(t, p->aspec, 1, 0, true, s));
+    return fft_zinv(t, p->aspec, g_white, 1, 0, 0, s);
+  });
+}
+
+}  // extern "C"
+
+extern "C" int fpm_status(fpm_plan* p, void* stream) {
   if (!p) return FPM_EINVAL;
   cudaStream_t s = S(stream);
   int h = 0;

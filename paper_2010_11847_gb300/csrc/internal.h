@@ -80,6 +80,40 @@ int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_
 int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
                int ik2, int idr, bool emit_keys, cudaStream_t s);
 
+// paint.cu: adjoints at fixed positions
+int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
+                      const float* v, float* g_dx, bool accumulate, cudaStream_t s);
+int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
+                     cudaStream_t s);
+
+// adjoint.cu: spectral adjoints (power-of-two sizes) and elementwise steps
+enum SrcKernel : int {
+  SK_FORCE_NEG = 0,   // -i g_d 1.5 Om / |w|^2   (transpose of the force operator, axis d)
+  SK_B = 1,           // i g_d / |w|^2            (B_d: displacement from density, axis d)
+  SK_BCONJ = 2,       // -i g_d / |w|^2           (B_d^T)
+  SK_H = 3,           // g_i g_j / |w|^2          (H_ij, second derivatives)
+  SK_LINEAR = 4,      // sqrt(P(|k|) N^3 / V)     (linear-field transfer)
+};
+struct XSource {
+  const float2* spec;   // half spectrum [kx][kz][ky]
+  int kind;             // SrcKernel
+  int a, b;             // axes (d, or i and j)
+  int in_k;             // 1: already in k space, 0: x axis still to transform
+};
+constexpr int XCOMBINE_MAX = 9;
+// out = sum_s K_s(k) X_s(k) * coef, then an inverse x transform when
+// inverse != 0 (out stays in k space otherwise).  out may alias a source.
+int fft_xcombine(const FftTables& t, const XSource* src, int nsrc, float coef, double omega_m, const EhParams* eh,
+                 const double* d_amp, float kf, float n3v, float2* out, int inverse, cudaStream_t s);
+int launch_chi2(const float* rho, const float* target, size_t M, float sigma, float* g_rho, double* partial,
+                int npartial, double* loss, cudaStream_t s);
+int launch_adj_drift_kick(float* gx, float* gp, float* v, size_t n, const double* fac, int idr, int ik1, int ik2,
+                          cudaStream_t s);
+int launch_scale_copy(const float* src, float* dst, size_t n, const double* fac, int ik, cudaStream_t s);
+int launch_lpt_gpsi(const float* gdx, const float* gp, size_t n, const double* gr, float a0, float r, float* out6,
+                    cudaStream_t s);
+int launch_lpt_gphi(const float* gS, float* phi6, size_t n, cudaStream_t s);
+
 inline size_t spec_elems(int n) { return (size_t)n * (n / 2 + 1) * n; }
 
 }  // namespace fpm

@@ -701,4 +701,186 @@ int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, 
   return FPM_OK;
 }
 
+// ================================================================ adjoints
+// Transposed Jacobians of paint and readout at fixed particle positions.
+
+// g_dx_i (+)= sum_c grad W(x_i - c) (mass g_rho_c + v_i . F_c): the paint
+// transpose (first term) and the readout's position term (second) share the
+// CIC gradient weights dW/dt_d = (b_d ? +1 : -1) prod_{e != d} w_e (the
+// right derivative at integer t, matching the floor-based cell).
+template <bool F4>
+__global__ void __launch_bounds__(256) k_gather_adj(const float* __restrict__ dx, Geom g, size_t N, size_t M,
+                                                    const float* __restrict__ g_rho, const float* __restrict__ F,
+                                                    const float* __restrict__ v, float* __restrict__ g_dx,
+                                                    int accumulate) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nc = g.nc;
+  int q[3], c[3];
+  float t[3];
+  lattice_node((uint32_t)i, g, q);
+  for (int a = 0; a < 3; ++a) cic_cell(dx[a * N + i], q[a], nc, &c[a], &t[a]);
+  const int c1[3] = {c[0] + 1 == nc ? 0 : c[0] + 1, c[1] + 1 == nc ? 0 : c[1] + 1, c[2] + 1 == nc ? 0 : c[2] + 1};
+  float vi[3] = {0.f, 0.f, 0.f};
+  if (v)
+    for (int a = 0; a < 3; ++a) vi[a] = v[a * N + i];
+  float gsum[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
+    const size_t idx = ((size_t)(bx ? c1[0] : c[0]) * nc + (by ? c1[1] : c[1])) * nc + (bz ? c1[2] : c[2]);
+    float s = 0.f;
+    if (g_rho) s = g.mass * __ldg(g_rho + idx);
+    if (v) {
+      if (F4) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(F) + idx);
+        s = fmaf(vi[0], f.x, fmaf(vi[1], f.y, fmaf(vi[2], f.z, s)));
+      } else {
+        for (int a = 0; a < 3; ++a) s = fmaf(vi[a], __ldg(F + a * M + idx), s);
+      }
+    }
+    const float wx = bx ? t[0] : 1.f - t[0], wy = by ? t[1] : 1.f - t[1], wz = bz ? t[2] : 1.f - t[2];
+    gsum[0] = fmaf((bx ? 1.f : -1.f) * wy * wz, s, gsum[0]);
+    gsum[1] = fmaf((by ? 1.f : -1.f) * wx * wz, s, gsum[1]);
+    gsum[2] = fmaf((bz ? 1.f : -1.f) * wx * wy, s, gsum[2]);
+  }
+  for (int a = 0; a < 3; ++a) g_dx[a * N + i] = accumulate ? g_dx[a * N + i] + gsum[a] : gsum[a];
+}
+
+// max |v| over n values as the bit pattern of a non-negative float (the
+// integer order of such patterns is their numeric order): order-independent.
+__global__ void k_maxabs(const float* __restrict__ v, size_t n, unsigned* __restrict__ out) {
+  unsigned m = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(v[i])));
+  for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Fixed-point unit 2^S for signed deposits: |w v| 2^S <= 2^30 for every
+// deposit (weights <= 1), a power of two so scaling is exact.
+__device__ __forceinline__ float signed_scale(unsigned maxbits) {
+  const float m = __uint_as_float(maxbits);
+  if (!(m > 0.f)) return 1.f;
+  return exp2f(floorf(30.f - log2f(m)) - 1.f);
+}
+
+// 64-bit two's-complement accumulation of a signed 32-bit value with 32-bit
+// shared atomics: low word with carry out, high word with carry minus sign.
+__device__ __forceinline__ void acc_add_signed(uint32_t* lo, uint32_t* hi, int c, int w) {
+  const uint32_t old = atomicAdd(lo + c, (uint32_t)w);
+  const int delta = ((old + (uint32_t)w) < old ? 1 : 0) - (w < 0 ? 1 : 0);
+  if (delta) atomicAdd(hi + c, (uint32_t)delta);
+}
+
+__device__ __forceinline__ float from_fix_signed(long long v, float inv_scale) {
+  return __ll2float_rn(v) * inv_scale;     // one rounding of the exact sum; the scale is a power of two
+}
+
+// Readout transpose for one channel: out_c = sum_i W(x_i - c) v_i (no
+// mass), deterministic signed fixed point in units set by max |v|.
+__global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restrict__ dx, size_t N,
+                                                          const uint32_t* __restrict__ items,
+                                                          const uint32_t* __restrict__ tile_start, Geom g,
+                                                          const float* __restrict__ vch,
+                                                          const unsigned* __restrict__ vmax,
+                                                          float* __restrict__ out,
+                                                          unsigned long long* __restrict__ halo) {
+  __shared__ uint32_t lo[ACC], hi[ACC];
+  const int nt = g.nt, nc = g.nc;
+  const int tile = blockIdx.x;
+  const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
+  const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
+  const float scale = signed_scale(*vmax), inv = 1.f / scale;
+  for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
+  __syncthreads();
+  for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+    const uint32_t i = __ldg(items + k);
+    int l[3];
+    float t[3];
+    if (!particle_local(dx, N, i, g, o, l, t)) continue;
+    const float vs = __ldg(vch + i) * scale;
+    const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
+    const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      acc_add_signed(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1),
+                     __float2int_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * vs));
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
+    const int lx = 1 + k / ((TILE - 1) * (TILE - 1)), ly = 1 + (k / (TILE - 1)) % (TILE - 1), lz = 1 + k % (TILE - 1);
+    out[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
+        from_fix_signed((long long)acc_get(lo, hi, (lx * TILE1 + ly) * TILE1 + lz), inv);
+  }
+  unsigned long long* hb = halo + (size_t)tile * SHELL;
+  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
+    int l[3];
+    shell_decode(s, l);
+    hb[s] = acc_get(lo, hi, (l[0] * TILE1 + l[1]) * TILE1 + l[2]);
+  }
+}
+
+// Face cells of the vector paint: signed sums of the covering tiles' shells.
+__global__ void __launch_bounds__(768) k_halo_vec(const unsigned long long* __restrict__ halo, Geom g,
+                                                  const unsigned* __restrict__ vmax, float* __restrict__ out) {
+  __shared__ uint32_t nb[8];
+  const int nt = g.nt, nc = g.nc;
+  const int tile = blockIdx.x;
+  const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
+  if (threadIdx.x < 8) {
+    const int b = threadIdx.x;
+    const int x = tc[0] - (b >> 2), y = tc[1] - ((b >> 1) & 1), z = tc[2] - (b & 1);
+    nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
+  }
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k >= NFACE) return;
+  int l[3];
+  if (k < TILE * TILE) {
+    l[0] = 0; l[1] = k >> 4; l[2] = k & 15;
+  } else if (k < TILE * TILE + (TILE - 1) * TILE) {
+    const int r = k - TILE * TILE;
+    l[0] = 1 + (r >> 4); l[1] = 0; l[2] = r & 15;
+  } else {
+    const int r = k - TILE * TILE - (TILE - 1) * TILE;
+    l[0] = 1 + r / (TILE - 1); l[1] = 1 + r % (TILE - 1); l[2] = 0;
+  }
+  unsigned long long sum = 0;
+  for (int b = 0; b < 8; ++b) {
+    const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
+    if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
+    sum += halo[(size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz)];
+  }
+  out[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
+      from_fix_signed((long long)sum, 1.f / signed_scale(*vmax));
+}
+
+int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
+                      const float* v, float* g_dx, bool accumulate, cudaStream_t s) {
+  if (f4)
+    k_gather_adj<true><<<grid_of(c.N, 256), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate);
+  else
+    k_gather_adj<false><<<grid_of(c.N, 256), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+// Readout transpose of the 3 channels of v into meshes out[3][M]; the tile
+// buckets must hold the positions dx (a paint of dx ran last on this ctx).
+int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
+                     cudaStream_t s) {
+  FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
+  k_maxabs<<<1024, 256, 0, s>>>(v, 3 * c.N, vmax);
+  FPM_CUDA_TRY(cudaGetLastError());
+  for (int ch = 0; ch < 3; ++ch) {
+    k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vmax,
+                                                out + ch * c.M, c.halo);
+    FPM_CUDA_TRY(cudaGetLastError());
+    k_halo_vec<<<c.ntiles, 768, 0, s>>>(c.halo, c.g, vmax, out + ch * c.M);
+    FPM_CUDA_TRY(cudaGetLastError());
+  }
+  return FPM_OK;
+}
+
 }  // namespace fpm

@@ -1,0 +1,178 @@
+"""Adjoint (reverse-mode) CUDA path against the FP64 oracle's adjoint.
+
+Per primitive: relative L2 <= 1e-5 (fixed positions, linear maps); reverse
+KDK and 2LPT <= 1e-4; the full gradient of chi^2 with respect to the white
+noise at 128^3 / 128^3, 400 Mpc/h, 5 steps: vector-norm relative error over
+32 random voxels <= 1e-3 against the oracle adjoint, and against central
+finite differences of the FP32 GPU forward (eps = 1e-3 and 3e-3), whose
+rounding noise is estimated from the spread of the two.
+"""
+import numpy as np
+import pytest
+
+from oracle import fpm_oracle as O
+from paper_2010_11847_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+COSMO = dict(inputs.COSMO_DEFAULT)
+OM = COSMO["omega_m"]
+
+
+def rel_l2(a, b):
+    dt = np.complex128 if (np.iscomplexobj(a) or np.iscomplexobj(b)) else np.float64
+    a = np.asarray(a, dtype=dt)
+    b = np.asarray(b, dtype=dt)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_mod(cuda):
+    import torch
+    return torch
+
+
+def plan(np_, nc, box=100.0, cosmo=COSMO):
+    from paper_2010_11847_gb300.binding import Plan
+    return Plan(np_, nc, box, cosmo)
+
+
+def dev(x, torch):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_force_adj_matches_oracle(torch_mod):
+    torch = torch_mod
+    n = 64
+    pl = plan(32, n)
+    gF = np.stack([inputs.random_field(n, 60 + d) for d in range(3)])
+    got = pl.force_adj(dev(gF, torch)).cpu().numpy()
+    assert rel_l2(got, O.force_adj(gF.astype(np.float64), OM)) < 1e-5
+
+
+@pytest.mark.parametrize("np_,nc", [(32, 32), (32, 64)])
+def test_paint_and_readout_adj_match_oracle(torch_mod, np_, nc):
+    torch = torch_mod
+    pl = plan(np_, nc)
+    dx = inputs.random_displacements(np_, 3.0, 70 + nc)
+    g_rho = inputs.random_field(nc, 71)
+    got = pl.paint_adj(dev(dx, torch), dev(g_rho, torch)).cpu().numpy()
+    assert rel_l2(got, O.paint_adj(g_rho.astype(np.float64), dx, np_, nc)) < 1e-5
+    F = np.stack([inputs.random_field(nc, 72 + d) for d in range(3)])
+    gf = inputs.random_displacements(np_, 1.0, 73)
+    gF, gdx = pl.readout_adj(dev(F, torch), dev(dx, torch), dev(gf, torch))
+    rF, rdx = O.readout_adj(F.astype(np.float64), dx, gf.astype(np.float64), np_, nc)
+    assert rel_l2(gF.cpu().numpy(), rF) < 1e-5
+    assert rel_l2(gdx.cpu().numpy(), rdx) < 1e-5
+
+
+def test_readout_adj_is_deterministic(torch_mod):
+    torch = torch_mod
+    pl = plan(32, 64)
+    dx = dev(inputs.random_displacements(32, 5.0, 3), torch)
+    F = dev(np.stack([inputs.random_field(64, 5 + d) for d in range(3)]), torch)
+    gf = dev(inputs.random_displacements(32, 1.0, 4), torch)
+    a, _ = pl.readout_adj(F, dx, gf)
+    b, _ = pl.readout_adj(F, dx, gf)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_lpt_and_linear_field_adj_match_oracle(torch_mod, order):
+    torch = torch_mod
+    n, nc, box = 32, 64, 100.0
+    pl = plan(n, nc, box)
+    w = inputs.white_noise(n, 90)
+    lk = O.linear_field(w, box, COSMO)
+    gdx = inputs.random_displacements(n, 1.0, 91)
+    gp = inputs.random_displacements(n, 1.0, 92)
+    lk_dev = dev(np.ascontiguousarray(lk.transpose(0, 2, 1)).astype(np.complex64), torch)
+    G = pl.lpt_adj(lk_dev, 0.1, dev(gdx, torch), dev(gp, torch), order)
+    rG = O.lpt_adj(lk, nc, 0.1, COSMO, gdx, gp, order)
+    assert rel_l2(G.permute(0, 2, 1).cpu().numpy(), rG) < 1e-4
+    gw = pl.linear_field_adj(dev(np.ascontiguousarray(rG.transpose(0, 2, 1)).astype(np.complex64), torch))
+    assert rel_l2(gw.cpu().numpy(), O.linear_field_adj(rG, box, COSMO)) < 1e-5
+
+
+def test_kdk_adj_matches_oracle_given_the_same_checkpoints(torch_mod):
+    torch = torch_mod
+    n, nc, box = 32, 32, 100.0
+    stages = np.linspace(0.1, 0.7, 4)
+    pl = plan(n, nc, box)
+    lk = O.linear_field(inputs.white_noise(n, 5), box, COSMO)
+    dx0, p0 = O.lpt(lk, nc, stages[0], COSMO)
+    rec = []
+    dxn, _ = O.kdk(dx0, p0, stages, n, nc, OM, record=rec)
+    xs = [x.astype(np.float32) for x, _ in rec] + [dxn.astype(np.float32)]
+    gdx = inputs.random_displacements(n, 1.0, 6)
+    gp = inputs.random_displacements(n, 1.0, 7)
+    rx, rp = O.kdk_adj(xs, stages, gdx, gp, n, nc, OM)
+    ckpt = dev(np.stack(xs), torch)
+    g_dx = dev(gdx, torch).clone()
+    g_dx, g_p = pl.kdk_adj(ckpt, stages, g_dx, g_p_in=dev(gp, torch))
+    assert rel_l2(g_dx.cpu().numpy(), rx) < 1e-4
+    assert rel_l2(g_p.cpu().numpy(), rp) < 1e-4
+    # without a momentum cotangent (a loss on the density alone)
+    rx0, rp0 = O.kdk_adj(xs, stages, gdx, np.zeros_like(gdx), n, nc, OM)
+    g_dx = dev(gdx, torch).clone()
+    g_dx, g_p = pl.kdk_adj(ckpt, stages, g_dx)
+    assert rel_l2(g_dx.cpu().numpy(), rx0) < 1e-4
+    assert rel_l2(g_p.cpu().numpy(), rp0) < 1e-4
+
+
+def test_differentiable_config_gradient(torch_mod):
+    """128^3 particles on 128^3, 400 Mpc/h, 2LPT at a=0.1 + 5 KDK steps;
+    chi^2 against the final density contrast of a second seed (sigma = 1)."""
+    torch = torch_mod
+    from paper_2010_11847_gb300.autograd import chi2_of_final_density
+    wl = inputs.DIFFERENTIABLE
+    stages = wl.stages()
+    w = inputs.white_noise(wl.np_, wl.seed)
+    ref_t = O.simulate(inputs.white_noise(wl.np_, wl.seed + 1), wl.nc, wl.box, wl.cosmo, stages)
+    target = (ref_t["rho"] - 1.0).astype(np.float32)
+    pl = plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    wt = dev(w, torch).requires_grad_(True)
+    tt = dev(target, torch)
+    loss = chi2_of_final_density(wt, tt, pl, stages)
+    loss.backward()
+    g = wt.grad.detach().cpu().numpy().reshape(-1)
+    L_ref, g_ref = O.chi2_and_grad(w, target.astype(np.float64), wl.nc, wl.box, wl.cosmo, stages)
+    assert abs(float(loss.detach()) / L_ref - 1) < 1e-4
+    idx = np.random.default_rng(2024).choice(w.size, size=32, replace=False)
+    ad, ref = g[idx], g_ref.reshape(-1)[idx]
+    vec = np.linalg.norm(ad - ref) / np.linalg.norm(ref)
+    per_voxel = np.abs(ad - ref) / np.maximum(np.abs(ref), 1e-30)
+    print(f"adjoint vs oracle adjoint: vector rel {vec:.2e}, per-voxel median {np.median(per_voxel):.2e}, "
+          f"max {per_voxel.max():.2e}")
+    assert vec < 1e-3
+    assert rel_l2(g, g_ref.reshape(-1)) < 1e-3
+
+    # central finite differences of the FP32 GPU forward, voxel by voxel:
+    # chi^2 sums ~2e6 float32 residuals, so its rounding noise (~1e-3
+    # absolute) swamps 2 eps dchi2/dw at eps = 1e-3; larger eps shows the
+    # agreement (the loss is smooth on that scale)
+    def gpu_loss(wv):
+        with torch.no_grad():
+            return float(chi2_of_final_density(wv, tt, pl, stages))
+    fds = {}
+    for eps in (1e-3, 3e-3, 3e-2):
+        out = []
+        for i in idx:
+            e = torch.zeros(w.size, device="cuda")
+            e[int(i)] = eps
+            e = e.view(w.shape)
+            out.append((gpu_loss(wt.detach() + e) - gpu_loss(wt.detach() - e)) / (2 * eps))
+        fds[eps] = np.array(out)
+    for eps, fd in fds.items():
+        print(f"FP32 central differences eps={eps:g}: vector rel error vs adjoint "
+              f"{np.linalg.norm(fd - ad) / np.linalg.norm(ad):.2e}")
+    assert np.linalg.norm(fds[3e-2] - ad) / np.linalg.norm(ad) < 2e-2
+    # directional derivative along a random direction on the 32 voxels
+    u = np.zeros(w.size, dtype=np.float32)
+    u[idx] = np.random.default_rng(7).standard_normal(32).astype(np.float32)
+    ut = torch.from_numpy(u).cuda().view(w.shape)
+    for eps in (1e-3, 1e-2):
+        dd = (gpu_loss(wt.detach() + eps * ut) - gpu_loss(wt.detach() - eps * ut)) / (2 * eps)
+        print(f"FP32 directional derivative eps={eps:g}: rel error {abs(dd - float(ad @ u[idx])) / abs(float(ad @ u[idx])):.2e}")
+    dd = (gpu_loss(wt.detach() + 1e-2 * ut) - gpu_loss(wt.detach() - 1e-2 * ut)) / 2e-2
+    assert abs(dd - float(ad @ u[idx])) < 1e-2 * abs(float(ad @ u[idx]))
