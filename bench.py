@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-simulation batched measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+adjoint measurements")
     ap.add_argument("--profile-json", default=None, help="write the per-class timing here")
     return ap.parse_args()
 
@@ -225,6 +227,98 @@ def ncu_traffic(cls):
     return None if e is None else e.get("dram_bytes_per_launch_full_size")
 
 
+def measure_batched(reps=3):
+    """64 simulations (meshes 32/64/96/128, 16 each, own cosmologies, 10 KDK
+    steps) by the persistent batched step, autotuned, against the same 64 runs
+    launched one by one.  Each run starts from its own 2LPT initial state."""
+    import torch
+    from paper_2010_11847_gb300 import inputs, autotune
+    from paper_2010_11847_gb300.binding import Plan, Batch
+    wls = inputs.batched_workloads()
+    plans, d0, p0 = [], [], []
+    for wl in wls:
+        pl = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+        lk = pl.linear_field(torch.from_numpy(inputs.white_noise(wl.np_, wl.seed)).cuda())
+        dx, p = pl.lpt(lk, wl.a0, 2)
+        plans.append(pl)
+        d0.append(dx)
+        p0.append(p)
+    a = wls[0].stages()
+    dxs = [x.clone() for x in d0]
+    ps = [x.clone() for x in p0]
+    b = Batch(plans)
+    tuned = autotune.tune(b, dxs, ps, a)
+
+    def reset():
+        for x, y, x0, y0 in zip(dxs, ps, d0, p0):
+            x.copy_(x0)
+            y.copy_(y0)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            reset()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    t_batch = timed(lambda: b.kdk(dxs, ps, a))
+    assert b.status() == 0
+    t_one = timed(lambda: [pl.kdk(x, y, a) for pl, x, y in zip(plans, dxs, ps)])
+    nps = sum(wl.np_ ** 3 for wl in wls) * wls[0].nsteps
+    info = b.info()
+    return {"workload": "batch64_mixed_32_64_96_128_10step", "sims": len(wls), "kdk_steps": wls[0].nsteps,
+            "ms_per_batched_run": t_batch, "ms_per_one_by_one_run": t_one, "speedup": t_one / t_batch,
+            "particle_steps_per_s_batched": nps / (t_batch / 1e3),
+            "launches_per_step": 1, "graph_captured": info["graph_captured"], "grid_blocks": info["grid_blocks"],
+            "autotune": tuned["config"], "autotune_cached": tuned["cached"]}
+
+
+def measure_fwd_adjoint(wl, reps=1):
+    """Forward + hand-written adjoint (d chi^2 / d white) of workload wl,
+    with dx checkpointed at every stage; ms per iteration and per PM step."""
+    import numpy as np
+    import torch
+    from paper_2010_11847_gb300 import inputs
+    from paper_2010_11847_gb300.binding import Plan
+    from paper_2010_11847_gb300.autograd import chi2_of_final_density
+    pl = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    stages = wl.stages()
+    w = torch.from_numpy(inputs.white_noise(wl.np_, wl.seed)).cuda()
+    target = torch.zeros(wl.nc, wl.nc, wl.nc, device="cuda")
+
+    def fwd_only():
+        lk = pl.linear_field(w)
+        dx, p = pl.lpt(lk, float(stages[0]), 2)
+        pl.kdk(dx, p, stages)
+        return pl.paint(dx)
+
+    def fwd_adj():
+        wt = w.clone().requires_grad_(True)
+        loss = chi2_of_final_density(wt, target, pl, stages)
+        loss.backward()
+        return wt.grad
+
+    out = {}
+    for name, fn in (("fwd", fwd_only), ("fwd_adj", fwd_adj)):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        out[name] = 1e3 * (time.perf_counter() - t0) / reps
+    pl.close()
+    return {"workload": wl.name, "ms_fwd": out["fwd"], "ms_fwd_adj": out["fwd_adj"],
+            "ms_per_pm_step_fwd_adj": out["fwd_adj"] / wl.nsteps, "ratio_fwd_adj_to_fwd": out["fwd_adj"] / out["fwd"],
+            "particle_steps_per_s_fwd_adj": wl.np_ ** 3 * wl.nsteps / (out["fwd_adj"] / 1e3)}
+
+
 def run_fpm(args):
     import numpy as np
     import torch
@@ -336,6 +430,19 @@ def run_fpm(args):
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
                 "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
     cpu = None if args.no_cpu_baseline else oracle_sample()
+    extra = {}
+    if not args.no_adjoint and args.workload == "large":
+        plan.close()
+        del dx, p, rho, lin_k
+        torch.cuda.empty_cache()
+        from paper_2010_11847_gb300 import inputs as _in
+        extra["fwd_adjoint"] = measure_fwd_adjoint(wl)
+        # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
+        # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
+        extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)
+        torch.cuda.empty_cache()
+    if not args.no_batch:
+        extra["batched"] = measure_batched()
     breakdown = {k: {"ms_per_sim": v[0] / args.steps, "launches_per_sim": v[1] / args.steps} for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,6 +464,7 @@ def run_fpm(args):
         "clocks": clk,
         "breakdown": breakdown,
     }
+    line.update(extra)
     if args.profile_json:
         json.dump(line, open(args.profile_json, "w"), indent=1)
     print(json.dumps(line))

@@ -200,6 +200,43 @@ int fpm_lpt_adj(fpm_plan* plan, const void* lin_k, double a0, int order, const f
  * g_white = IDFT(s g_lin_k) (float[np^3]). */
 int fpm_linear_field_adj(fpm_plan* plan, const void* g_lin_k, float* g_white, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batched simulations.  Many independent simulations (each with its own
+ * plan: size, box, cosmology) advance together by one persistent
+ * cooperative kernel launch per KDK step; a launch runs every phase of the
+ * step (readout-kick-drift and keys, tile scan, scatter, paint, halo, the
+ * five FFT passes with the force transfer function) over a work list that
+ * spans all simulations, with a bounded-spin grid barrier between phases
+ * (FPM_ETIMEOUT instead of a hang).  A whole run is captured once into a
+ * CUDA graph and replayed.  The paper's batch splitting (Sec. 4) is the
+ * use case; each simulation gives the same bits as fpm_kdk on its plan.
+ * Supported plans: np = nc in {32, 64, 96, 128}.
+ * ------------------------------------------------------------------- */
+typedef struct fpm_batch fpm_batch;
+
+/* Group nsims plans (HOST array of plan pointers; the plans must outlive the
+ * batch and are used as the simulations' scratch). */
+int fpm_batch_create(fpm_batch** batch, fpm_plan* const* plans, int nsims);
+void fpm_batch_destroy(fpm_batch* batch);
+
+/* Tuning knobs (negative / zero: keep): persistent blocks per SM (0 = as
+ * many as fit), 256-particle chunks per readout work item, barrier spin
+ * limit (iterations of a ~64 ns sleep before FPM_ETIMEOUT). */
+int fpm_batch_configure(fpm_batch* batch, int blocks_per_sm, int readout_chunks, int64_t spin_limit);
+
+/* Run nsteps KDK steps of every simulation between the HOST scale factors
+ * a[0..nsteps] (shared by all), updating dx[s], p[s] in place (HOST arrays
+ * of device pointers, float[3][np_s^3] each), exactly as fpm_kdk would. */
+int fpm_batch_kdk(fpm_batch* batch, float* const* dx, float* const* p, const double* a, int nsteps,
+                  void* stream);
+
+/* FPM_ETIMEOUT if a grid barrier gave up, else the plans' device flags;
+ * synchronises `stream` and clears the flags. */
+int fpm_batch_status(fpm_batch* batch, void* stream);
+
+/* Persistent grid size in blocks, and whether the run was graph-captured. */
+int fpm_batch_info(fpm_batch* batch, int* grid_blocks, int* graph_captured);
+
 /* CIC paint that allocates nothing (the paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc -- code running while a
  * stream is captured into a CUDA graph, loops that cannot afford

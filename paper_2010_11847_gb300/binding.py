@@ -25,7 +25,8 @@ EXPORTS = [
     "fpm_lpt", "fpm_paint", "fpm_force", "fpm_readout", "fpm_kdk", "fpm_power", "fpm_status", "fpm_strerror",
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
     "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
-    "fpm_linear_field_adj",
+    "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
+    "fpm_batch_status", "fpm_batch_info",
 ]
 FPM_K_COUNT = 15
 
@@ -80,9 +81,16 @@ def lib() -> ctypes.CDLL:
     L.fpm_kdk_adj.argtypes = [vp, vp, vp, i, vp, vp, vp, vp]
     L.fpm_lpt_adj.argtypes = [vp, vp, d, i, vp, vp, vp, vp]
     L.fpm_linear_field_adj.argtypes = [vp, vp, vp, vp]
+    L.fpm_batch_create.argtypes = [ctypes.POINTER(vp), vp, i]
+    L.fpm_batch_destroy.argtypes = [vp]
+    L.fpm_batch_destroy.restype = None
+    L.fpm_batch_configure.argtypes = [vp, i, i, i64]
+    L.fpm_batch_kdk.argtypes = [vp, vp, vp, vp, i, vp]
+    L.fpm_batch_status.argtypes = [vp, vp]
+    L.fpm_batch_info.argtypes = [vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_strerror", "fpm_kernel_class_name",
-                        "fpm_launch_count"):
+                        "fpm_launch_count", "fpm_batch_destroy"):
             getattr(L, name).restype = i
     _LIB = L
     return L
@@ -277,6 +285,48 @@ class Plan:
         dx, p = self.lpt(lin_k, float(a[0]), order, stream=stream)
         self.kdk(dx, p, a, ckpt=ckpt, stream=stream)
         return dx, p, lin_k
+
+
+class Batch:
+    """An fpm_batch: independent simulations (one Plan each) advanced by one
+    persistent launch per KDK step, graph-captured."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check("fpm_batch_create", lib().fpm_batch_create(ctypes.byref(h), arr, len(self.plans)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fpm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, blocks_per_sm=-1, readout_chunks=-1, spin_limit=-1):
+        _check("fpm_batch_configure", lib().fpm_batch_configure(self._h, int(blocks_per_sm), int(readout_chunks),
+                                                                int(spin_limit)))
+
+    def kdk(self, dxs, ps, a, stream=None):
+        a = _host_f64(a).ravel()
+        dptr = (ctypes.c_void_p * len(dxs))(*[_ptr(x) for x in dxs])
+        pptr = (ctypes.c_void_p * len(ps))(*[_ptr(x) for x in ps])
+        _check("fpm_batch_kdk", lib().fpm_batch_kdk(self._h, dptr, pptr, a.ctypes.data, a.size - 1,
+                                                    _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        return int(lib().fpm_batch_status(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        g, c = ctypes.c_int(), ctypes.c_int()
+        _check("fpm_batch_info", lib().fpm_batch_info(self._h, ctypes.byref(g), ctypes.byref(c)))
+        return {"grid_blocks": g.value, "graph_captured": bool(c.value)}
 
 
 def paint_noalloc(np_: int, nc: int, dx, rho, stream=None):

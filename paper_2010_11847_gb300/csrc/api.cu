@@ -651,6 +651,87 @@ int fpm_linear_field_adj(fpm_plan* p, const void* g_lin_k, float* g_white, void*
   });
 }
 
+// ---------------------------------------------------------------- batched
+struct fpm_batch {
+  Batch* impl = nullptr;
+  std::vector<fpm_plan*> plans;
+};
+
+int fpm_batch_create(fpm_batch** out, fpm_plan* const* plans, int nsims) {
+  if (!out || !plans || nsims < 1 || nsims > 4096) return FPM_EINVAL;
+  std::vector<BatchPlanView> views(nsims);
+  for (int s = 0; s < nsims; ++s) {
+    fpm_plan* p = plans[s];
+    if (!p || !batch_size_ok(p->nc, p->np)) return FPM_EINVAL;
+    BatchPlanView& v = views[s];
+    v.pc = p->pc;
+    v.nc = p->nc;
+    v.np = p->np;
+    v.f4 = p->f4 ? 1 : 0;
+    v.F = p->F;
+    v.rho = p->rho;
+    v.spec = p->spec;
+    v.specmax = p->specmax;
+    v.fac = p->d_fac;
+    v.tab = p->tc;
+    v.force_coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
+  }
+  fpm_batch* b = new fpm_batch();
+  b->plans.assign(plans, plans + nsims);
+  const int rc = batch_create(&b->impl, views.data(), nsims);
+  if (rc != FPM_OK) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return FPM_OK;
+}
+
+void fpm_batch_destroy(fpm_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_destroy(b->impl);
+  delete b;
+}
+
+int fpm_batch_configure(fpm_batch* b, int blocks_per_sm, int readout_chunks, int64_t spin_limit) {
+  if (!b) return FPM_EINVAL;
+  return batch_configure(b->impl, blocks_per_sm, readout_chunks, (long long)spin_limit);
+}
+
+int fpm_batch_kdk(fpm_batch* b, float* const* dx, float* const* mom, const double* a, int nsteps, void* stream) {
+  if (!b || !dx || !mom || !a || nsteps < 1 || nsteps > MAX_STEPS) return FPM_EINVAL;
+  for (int k = 0; k <= nsteps; ++k)
+    if (!(a[k] > 1e-5 && a[k] <= 10.0) || (k > 0 && !(a[k] > a[k - 1]))) return FPM_EINVAL;
+  const int ns = (int)b->plans.size();
+  for (int s = 0; s < ns; ++s)
+    if (!dx[s] || !mom[s]) return FPM_EINVAL;
+  cudaStream_t s = S(stream);
+  std::vector<double> pts(a, a + nsteps + 1);
+  for (int k = 0; k < nsteps; ++k) pts.push_back(sqrt(a[k] * a[k + 1]));
+  for (fpm_plan* p : b->plans) {   // FP64 factors of every simulation's own cosmology
+    FPM_TRY(stage_points(p, pts.data(), (int)pts.size(), s));
+    FPM_TRY(launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s));
+    g_launches += 3;
+  }
+  FPM_TRY(batch_kdk(b->impl, dx, mom, nsteps, s));
+  g_launches += nsteps + 2;
+  return FPM_OK;
+}
+
+int fpm_batch_status(fpm_batch* b, void* stream) {
+  if (!b) return FPM_EINVAL;
+  const int rc = batch_status(b->impl, S(stream));
+  if (rc != FPM_OK) return rc;
+  for (fpm_plan* p : b->plans) FPM_TRY(fpm_status(p, stream));
+  return FPM_OK;
+}
+
+int fpm_batch_info(fpm_batch* b, int* grid_blocks, int* graph_captured) {
+  if (!b) return FPM_EINVAL;
+  return batch_info(b->impl, grid_blocks, graph_captured);
+}
+
 }  // extern "C"
 
 extern "C" int fpm_status(fpm_plan* p, void* stream) {

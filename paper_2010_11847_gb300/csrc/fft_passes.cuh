@@ -30,9 +30,8 @@ constexpr size_t xpass_smem(int nbuf) { return (size_t)(nbuf * XB * sp_size(N) +
 
 // ---------------------------------------------------------------- z r2c
 template <int N>
-__global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const float* __restrict__ in, float2* __restrict__ out,
-                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw) {
-  extern __shared__ float2 smem[];
+__device__ __forceinline__ void body_zfwd(const float* __restrict__ in, float2* __restrict__ out,
+                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   constexpr int LS = sp_size(N);
   constexpr int NH = N / 2 + 1;
   constexpr int GROUPS = N / (2 * ZG);
@@ -40,16 +39,16 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const float* __restrict__ 
   float2* b = a + ZG * LS;
   float2* tw = b + ZG * LS;
   load_twiddles<N>(tw, g_tw);
-  const int x = blockIdx.x / GROUPS;
-  const int y0 = (blockIdx.x % GROUPS) * 2 * ZG;
-  const float* src = in + blockIdx.y * in_fs + ((size_t)x * N + y0) * N;
+  const int x = bx / GROUPS;
+  const int y0 = (bx % GROUPS) * 2 * ZG;
+  const float* src = in + by * in_fs + ((size_t)x * N + y0) * N;
   for (int idx = threadIdx.x; idx < ZG * N; idx += blockDim.x) {
     const int g = idx / N, z = idx - g * N;
     a[g * LS + sp(z)] = make_float2(__ldg(src + (2 * g) * N + z), __ldg(src + (2 * g + 1) * N + z));
   }
   __syncthreads();
   const float2* r = FftPlan<N>::template run<false>(a, b, ZG, LS, tw);
-  float4* dst = reinterpret_cast<float4*>(out + blockIdx.y * out_fs + (size_t)x * NH * N + y0);
+  float4* dst = reinterpret_cast<float4*>(out + by * out_fs + (size_t)x * NH * N + y0);
   for (int idx = threadIdx.x; idx < NH * ZG; idx += blockDim.x) {
     const int kz = idx / ZG, g = idx - kz * ZG;
     const float2 zk = r[g * LS + sp(kz)];
@@ -60,19 +59,25 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const float* __restrict__ 
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const float* __restrict__ in, float2* __restrict__ out,
+                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_zfwd<N>(in, out, in_fs, out_fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- y (in place)
 template <int N, bool INV>
-__global__ void __launch_bounds__(FFT_THREADS) k_yfft(float2* __restrict__ data, int nlines, size_t fs,
-                                                      const float2* __restrict__ g_tw) {
-  extern __shared__ float2 smem[];
+__device__ __forceinline__ void body_yfft(float2* __restrict__ data, int nlines, size_t fs,
+                                                      const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   constexpr int LS = sp_size(N);
   float2* a = smem;
   float2* b = a + YL * LS;
   float2* tw = b + YL * LS;
   load_twiddles<N>(tw, g_tw);
-  const int line0 = blockIdx.x * YL;
+  const int line0 = bx * YL;
   const int nl = min(YL, nlines - line0);
-  float2* base = data + blockIdx.y * fs + (size_t)line0 * N;
+  float2* base = data + by * fs + (size_t)line0 * N;
   for (int idx = threadIdx.x; idx < YL * N; idx += blockDim.x) {
     const int l = idx / N, e = idx - l * N;
     a[l * LS + sp(e)] = (l < nl) ? base[(size_t)l * N + e] : make_float2(0.f, 0.f);
@@ -85,11 +90,17 @@ __global__ void __launch_bounds__(FFT_THREADS) k_yfft(float2* __restrict__ data,
   }
 }
 
+template <int N, bool INV>
+__global__ void __launch_bounds__(FFT_THREADS) k_yfft(float2* __restrict__ data, int nlines, size_t fs,
+                                                      const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_yfft<N, INV>(data, nlines, fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- z c2r
 template <int N>
-__global__ void __launch_bounds__(FFT_THREADS) k_zinv(const float2* __restrict__ in, float* __restrict__ out,
-                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw) {
-  extern __shared__ float2 smem[];
+__device__ __forceinline__ void body_zinv(const float2* __restrict__ in, float* __restrict__ out,
+                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   constexpr int LS = sp_size(N);
   constexpr int NH = N / 2 + 1;
   constexpr int GROUPS = N / (2 * ZG);
@@ -97,9 +108,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(const float2* __restrict__
   float2* b = a + ZG * LS;
   float2* tw = b + ZG * LS;
   load_twiddles<N>(tw, g_tw);
-  const int x = blockIdx.x / GROUPS;
-  const int y0 = (blockIdx.x % GROUPS) * 2 * ZG;
-  const float4* src = reinterpret_cast<const float4*>(in + blockIdx.y * in_fs + (size_t)x * NH * N + y0);
+  const int x = bx / GROUPS;
+  const int y0 = (bx % GROUPS) * 2 * ZG;
+  const float4* src = reinterpret_cast<const float4*>(in + by * in_fs + (size_t)x * NH * N + y0);
   for (int idx = threadIdx.x; idx < NH * ZG; idx += blockDim.x) {
     const int kz = idx / ZG, g = idx - kz * ZG;
     const float4 v = __ldg(src + ((size_t)kz * N) / 2 + g);   // A = (x, y), B = (z, w)
@@ -112,13 +123,20 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(const float2* __restrict__
   }
   __syncthreads();
   const float2* r = FftPlan<N>::template run<true>(a, b, ZG, LS, tw);
-  float* dst = out + blockIdx.y * out_fs + ((size_t)x * N + y0) * N;
+  float* dst = out + by * out_fs + ((size_t)x * N + y0) * N;
   for (int idx = threadIdx.x; idx < ZG * N; idx += blockDim.x) {
     const int g = idx / N, z = idx - g * N;
     const float2 v = r[g * LS + sp(z)];
     dst[(2 * g) * N + z] = v.x;
     dst[(2 * g + 1) * N + z] = v.y;
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_zinv(const float2* __restrict__ in, float* __restrict__ out,
+                                                      size_t in_fs, size_t out_fs, const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_zinv<N>(in, out, in_fs, out_fs, g_tw, smem, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- x pass helpers
@@ -147,11 +165,10 @@ __device__ __forceinline__ void xstore(float2* __restrict__ spec, const float2* 
 // for each axis d: F_d(k) = i g_d 1.5 Om delta(k) / |w|^2 (coef = 1.5 Om / M
 // folds in the inverse normalisation), inverse x transform.  out may alias in.
 template <int N>
-__global__ void __launch_bounds__(FFT_THREADS) k_xforce(const float2* in, float2* out, size_t out_fs,
+__device__ __forceinline__ void body_xforce(const float2* in, float2* out, size_t out_fs,
                                                         float coef, const float2* __restrict__ g_tw,
                                                         const float* __restrict__ g_g,
-                                                        const float* __restrict__ g_w2) {
-  extern __shared__ float2 smem[];
+                                                        const float* __restrict__ g_w2, float2* smem, int bx, int by) {
   constexpr int LS = sp_size(N);
   constexpr int NB = N / XB;
   float2* s0 = smem;
@@ -159,8 +176,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xforce(const float2* in, float2
   float2* s2 = s1 + XB * LS;
   float2* tw = s2 + XB * LS;
   load_twiddles<N>(tw, g_tw);
-  const int kz = blockIdx.x / NB;
-  const int ky0 = (blockIdx.x % NB) * XB;
+  const int kz = bx / NB;
+  const int ky0 = (bx % NB) * XB;
   xload<N>(s0, in, kz, ky0);
   __syncthreads();
   float2* d = FftPlan<N>::template run<false>(s0, s1, XB, LS, tw);
@@ -182,6 +199,15 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xforce(const float2* in, float2
     xstore<N>(out + axis * out_fs, r, kz, ky0);
     __syncthreads();
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_xforce(const float2* in, float2* out, size_t out_fs,
+                                                        float coef, const float2* __restrict__ g_tw,
+                                                        const float* __restrict__ g_g,
+                                                        const float* __restrict__ g_w2) {
+  extern __shared__ float2 smem[];
+  body_xforce<N>(in, out, out_fs, coef, g_tw, g_g, g_w2, smem, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fpm

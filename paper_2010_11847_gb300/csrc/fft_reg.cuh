@@ -104,18 +104,17 @@ struct RegCfg {
 // ---------------------------------------------------------------- z r2c
 // L complex lines = 2L consecutive real rows (row = x*N + y) per CTA.
 template <int N>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zfwd_r(const float* __restrict__ in,
+__device__ __forceinline__ void body_zfwd_r(const float* __restrict__ in,
                                                                float2* __restrict__ out, size_t in_fs,
-                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+                                                               size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   using C = RegCfg<N>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
-  extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* xb = tw + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
-  const size_t r0 = (size_t)blockIdx.x * 2 * L;
-  const float* src = in + blockIdx.y * in_fs + (r0 + 2 * g) * N;
+  const size_t r0 = (size_t)bx * 2 * L;
+  const float* src = in + by * in_fs + (r0 + 2 * g) * N;
   float2 v[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[s] = make_float2(__ldg(src + t + T * s), __ldg(src + N + t + T * s));
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
 #pragma unroll
   for (int s = 0; s < 8; ++s) buf[rp(t + T * s)] = v[s];
   __syncthreads();
-  float2* dst = out + blockIdx.y * out_fs;
+  float2* dst = out + by * out_fs;
   for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
     const int kz = idx / L, gg = idx - kz * L;
     const float2* b = xb + gg * rline<N>();
@@ -139,20 +138,27 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zfwd_r(const float* __restrict__ in,
+                                                               float2* __restrict__ out, size_t in_fs,
+                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_zfwd_r<N>(in, out, in_fs, out_fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- y (in place, contiguous lines)
 template <int N, bool INV>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_yfft_r(float2* __restrict__ data, int nlines, size_t fs,
-                                                               const float2* __restrict__ g_tw) {
+__device__ __forceinline__ void body_yfft_r(float2* __restrict__ data, int nlines, size_t fs,
+                                                               const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   using C = RegCfg<N>;
   constexpr int T = C::T, L = C::L;
-  extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* xb = tw + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
   const int line = threadIdx.x / T, t = threadIdx.x - line * T;
-  const int gl = blockIdx.x * L + line;
+  const int gl = bx * L + line;
   const bool valid = gl < nlines;
-  float2* base = data + blockIdx.y * fs + (size_t)gl * N;
+  float2* base = data + by * fs + (size_t)gl * N;
   float2 v[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[s] = valid ? base[t + T * s] : make_float2(0.f, 0.f);
@@ -164,19 +170,25 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
   }
 }
 
+template <int N, bool INV>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_yfft_r(float2* __restrict__ data, int nlines, size_t fs,
+                                                               const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_yfft_r<N, INV>(data, nlines, fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- z c2r
 template <int N>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zinv_r(const float2* __restrict__ in,
+__device__ __forceinline__ void body_zinv_r(const float2* __restrict__ in,
                                                                float* __restrict__ out, size_t in_fs,
-                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+                                                               size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   using C = RegCfg<N>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
-  extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* xb = tw + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
-  const size_t r0 = (size_t)blockIdx.x * 2 * L;
-  const float2* src = in + blockIdx.y * in_fs;
+  const size_t r0 = (size_t)bx * 2 * L;
+  const float2* src = in + by * in_fs;
   for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
     const int kz = idx / L, gg = idx - kz * L;
     const size_t row = r0 + 2 * gg;
@@ -198,7 +210,7 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
   for (int s = 0; s < 8; ++s) v[s] = buf[rp(t + T * s)];
   __syncthreads();
   RegFft<N>::template run<true>(v, buf, t, tw);
-  float* dst = out + blockIdx.y * out_fs + (r0 + 2 * g) * N;
+  float* dst = out + by * out_fs + (r0 + 2 * g) * N;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     dst[t + T * s] = v[s].x;
@@ -206,19 +218,25 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zinv_r(const float2* __restrict__ in,
+                                                               float* __restrict__ out, size_t in_fs,
+                                                               size_t out_fs, const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_zinv_r<N>(in, out, in_fs, out_fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // Three fields in one CTA, written interleaved as float4 (F0, F1, F2, 0)
 // per cell: the readout then fetches a CIC corner with one 16-byte load.
 template <int N>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
-    k_zinv3_r(const float2* __restrict__ in, float4* __restrict__ out, size_t in_fs,
-              const float2* __restrict__ g_tw) {
+__device__ __forceinline__ void body_zinv3_r(const float2* __restrict__ in, float4* __restrict__ out, size_t in_fs,
+              const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
   using C = RegCfg<N>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
-  extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* xb = tw + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
-  const size_t r0 = (size_t)blockIdx.x * 2 * L;
+  const size_t r0 = (size_t)bx * 2 * L;
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   float2* buf = xb + g * rline<N>();
   float2 res[3][8];
@@ -252,24 +270,30 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_zinv3_r(const float2* __restrict__ in, float4* __restrict__ out, size_t in_fs,
+              const float2* __restrict__ g_tw) {
+  extern __shared__ float2 smem[];
+  body_zinv3_r<N>(in, out, in_fs, g_tw, smem, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- x pass: force transfer function
 // L consecutive lines l = kz*N + ky per CTA (line fastest across threads);
 // forward x transform of delta(k), then per axis d the Eq. 3-5 operator
 // F_d = i g_d coef delta / |w|^2 and the inverse x transform, from registers.
 template <int N>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_xforce_r(const float2* in, float2* out, size_t out_fs,
+__device__ __forceinline__ void body_xforce_r(const float2* in, float2* out, size_t out_fs,
                                                                  float coef, const float2* __restrict__ g_tw,
                                                                  const float* __restrict__ g_g,
-                                                                 const float* __restrict__ g_w2) {
+                                                                 const float* __restrict__ g_w2, float2* smem, int bx, int by) {
   using C = RegCfg<N>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
   constexpr size_t S = (size_t)NH * N;
-  extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* xb = tw + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
   const int line = threadIdx.x % L, t = threadIdx.x / L;
-  const int gl = blockIdx.x * L + line;
+  const int gl = bx * L + line;
   const bool valid = gl < NH * N;
   const int kz = gl / N, ky = gl - kz * N;
   float2 d[8];
@@ -301,6 +325,15 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
       for (int s = 0; s < 8; ++s) o[(size_t)(t + T * s) * S + gl] = v[s];
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_xforce_r(const float2* in, float2* out, size_t out_fs,
+                                                                 float coef, const float2* __restrict__ g_tw,
+                                                                 const float* __restrict__ g_g,
+                                                                 const float* __restrict__ g_w2) {
+  extern __shared__ float2 smem[];
+  body_xforce_r<N>(in, out, out_fs, coef, g_tw, g_g, g_w2, smem, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fpm

@@ -114,6 +114,27 @@ int launch_lpt_gpsi(const float* gdx, const float* gp, size_t n, const double* g
                     cudaStream_t s);
 int launch_lpt_gphi(const float* gS, float* phi6, size_t n, cudaStream_t s);
 
+// batch.cu: many simulations, one persistent launch per step
+struct BatchPlanView {
+  PaintCtx pc;
+  int nc = 0, np = 0, f4 = 0;
+  float* F = nullptr;
+  float* rho = nullptr;
+  float2* spec = nullptr;
+  size_t specmax = 0;
+  const double* fac = nullptr;
+  FftTables tab;
+  float force_coef = 0.f;
+};
+struct Batch;
+bool batch_size_ok(int nc, int np);
+int batch_create(Batch** out, const BatchPlanView* views, int nsims);
+void batch_destroy(Batch* b);
+int batch_configure(Batch* b, int blocks_per_sm, int ro_iters, long long spin_limit);
+int batch_kdk(Batch* b, float* const* dx, float* const* p, int nsteps, cudaStream_t s);
+int batch_status(Batch* b, cudaStream_t s);
+int batch_info(const Batch* b, int* grid, int* graph_captured);
+
 inline size_t spec_elems(int n) { return (size_t)n * (n / 2 + 1) * n; }
 
 }  // namespace fpm

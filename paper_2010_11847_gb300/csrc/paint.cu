@@ -21,280 +21,30 @@
 // Cells that only this tile touches are written directly; the shell of the
 // 17^3 block goes to a per-tile halo buffer that a second kernel sums over
 // the (up to 8) tiles covering each face cell.
-#include "internal.h"
+#include "paint_dev.cuh"
 
 namespace fpm {
 
-constexpr int PB_THREADS = 512;     // paint CTA (bucket order)
-constexpr int PS_THREADS = 256;     // paint CTA (sorted order, permutation output)
-constexpr int PCAP = 8192;          // particles per tile sorted in shared memory
-constexpr int ACC = TILE1 * TILE1 * TILE1;
-constexpr size_t SORTED_SMEM = 2 * ACC * sizeof(uint32_t) + TILE3 * sizeof(uint32_t) + PCAP * sizeof(uint32_t);
-constexpr float W_ONE = 16777216.0f;              // 2^24: fixed-point unit of a CIC weight
-constexpr float W_INV = 5.9604644775390625e-08f;  // 2^-24
-constexpr int NFACE = TILE * TILE + (TILE - 1) * TILE + (TILE - 1) * (TILE - 1);   // 721 lower-face cells
+// ---------------------------------------------------------------- kernels
+constexpr int SCAN_THREADS = 1024;
 
-// Wrap c into [0, n) for |c| < 2^31 - n (one correction in the common case).
-__device__ __forceinline__ int wrapi(int c, int n) {
-  if (c < 0) c += n;
-  if (c >= n) c -= n;
-  if ((unsigned)c >= (unsigned)n) {
-    c %= n;
-    if (c < 0) c += n;
-  }
-  return c;
-}
-
-__device__ __forceinline__ void lattice_node(uint32_t i, const Geom& g, int* q) {
-  const uint32_t ix = fdiv(i, g.div_np2);
-  const uint32_t rem = i - ix * g.div_np2.d;
-  const uint32_t iy = fdiv(rem, g.div_np);
-  const uint32_t iz = rem - iy * g.div_np.d;
-  q[0] = ix * g.ratio;
-  q[1] = iy * g.ratio;
-  q[2] = iz * g.ratio;
-}
-
-// Base cell and fraction from a float32 displacement.  Returns false (and
-// the cell 0) for a non-finite or absurdly large displacement.
-__device__ __forceinline__ bool cic_cell(float d, int q, int nc, int* c, float* t) {
-  if (!(fabsf(d) < 1.0e7f)) {
-    *c = 0;
-    *t = 0.f;
-    return false;
-  }
-  const float fl = floorf(d);
-  *c = wrapi(q + (int)fl, nc);
-  *t = d - fl;
-  return true;
-}
-
-__device__ __forceinline__ uint32_t tile_key(const int* c, int nt) {
-  const uint32_t tile = ((uint32_t)(c[0] >> 4) * nt + (c[1] >> 4)) * nt + (c[2] >> 4);
-  const uint32_t local = ((c[0] & 15) * TILE + (c[1] & 15)) * TILE + (c[2] & 15);
-  return tile * TILE3 + local;
-}
-
-// Warp-aggregated increment of counter[bucket] for every active lane.
-__device__ __forceinline__ void warp_count(uint32_t* counter, int bucket, bool active) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int key = active ? bucket : -1 - lane;
-  const unsigned grp = __match_any_sync(full, key);
-  if (active && lane == __ffs(grp) - 1) atomicAdd(counter + bucket, (uint32_t)__popc(grp));
-}
-
-// ---------------------------------------------------------------- keys + tile histogram
 __global__ void k_keys(const float* __restrict__ dx, Geom g, size_t N, uint32_t* __restrict__ keys,
                        uint32_t* __restrict__ tile_count, int* __restrict__ err) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < N;
-  int tile = 0;
-  if (active) {
-    int q[3], c[3];
-    float t;
-    lattice_node((uint32_t)i, g, q);
-    bool ok = true;
-    for (int d = 0; d < 3; ++d) ok &= cic_cell(dx[d * N + i], q[d], g.nc, &c[d], &t);
-    if (!ok) atomicOr(err, ERR_NAN);
-    const uint32_t key = tile_key(c, g.nt);
-    keys[i] = key;
-    tile = key >> 12;
-  }
-  warp_count(tile_count, tile, active);
+  body_keys(dx, g, N, keys, tile_count, err, blockIdx.x);
 }
 
-// ---------------------------------------------------------------- scan of tile counts
-constexpr int SCAN_THREADS = 1024;
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* __restrict__ count, int ntiles,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(uint32_t* __restrict__ count, int ntiles,
                                                              uint32_t* __restrict__ start,
                                                              uint32_t* __restrict__ cursor) {
   __shared__ uint32_t part[SCAN_THREADS];
-  const int per = (ntiles + SCAN_THREADS - 1) / SCAN_THREADS;
-  const int b = threadIdx.x * per;
-  uint32_t s = 0;
-  for (int k = 0; k < per && b + k < ntiles; ++k) s += count[b + k];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < SCAN_THREADS; off <<= 1) {      // Hillis-Steele inclusive scan
-    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (int k = 0; k < per && b + k < ntiles; ++k) {
-    start[b + k] = run;
-    cursor[b + k] = run;
-    run += count[b + k];
-  }
-  if (threadIdx.x == SCAN_THREADS - 1) start[ntiles] = part[SCAN_THREADS - 1];
+  body_scan_tiles(count, ntiles, start, cursor, part, 0);
 }
 
-// ---------------------------------------------------------------- bucket by tile
-// Each thread places SCAT_E particles; the cursor atomics of its chunks are
-// issued back to back so their round trips to L2 overlap.
-constexpr int SCAT_E = 4;
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ keys, size_t N,
                                                  uint32_t* __restrict__ cursor, uint32_t* __restrict__ items) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const size_t i0 = (size_t)blockIdx.x * blockDim.x * SCAT_E + threadIdx.x;
-  int tile[SCAT_E];
-  unsigned grp[SCAT_E];
-  uint32_t base[SCAT_E];
-#pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    const size_t i = i0 + (size_t)e * blockDim.x;
-    tile[e] = i < N ? (int)(__ldg(keys + i) >> 12) : -1 - lane;
-    grp[e] = __match_any_sync(full, tile[e]);
-  }
-#pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    base[e] = 0;
-    if (tile[e] >= 0 && lane == __ffs(grp[e]) - 1) base[e] = atomicAdd(cursor + tile[e], (uint32_t)__popc(grp[e]));
-  }
-#pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    const uint32_t b = __shfl_sync(full, base[e], __ffs(grp[e]) - 1);
-    if (tile[e] >= 0) items[b + __popc(grp[e] & ((1u << lane) - 1u))] = (uint32_t)(i0 + (size_t)e * blockDim.x);
-  }
+  body_scatter(keys, N, cursor, items, blockIdx.x);
 }
 
-// ---------------------------------------------------------------- fixed point
-__device__ __forceinline__ float from_fix(unsigned long long v, float mass) {
-  const float hi = (float)(uint32_t)(v >> 32);
-  const float lo = (float)(uint32_t)(v & 0xffffffffull);
-  return fmaf(hi, 256.0f, lo * W_INV) * mass;                // (hi 2^32 + lo) 2^-24
-}
-
-// Exact 64-bit accumulation with 32-bit shared atomics: the thread whose
-// add wraps the low word carries into the high word.
-__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int c, uint32_t w) {
-  const uint32_t old = atomicAdd(lo + c, w);
-  if (old + w < old) atomicAdd(hi + c, 1u);
-}
-
-__device__ __forceinline__ unsigned long long acc_get(const uint32_t* lo, const uint32_t* hi, int c) {
-  return ((unsigned long long)hi[c] << 32) | lo[c];
-}
-
-__device__ __forceinline__ int shell_index(int lx, int ly, int lz) {
-  // cells of the 17^3 block with a coordinate in {0, 16}
-  if (lx == 0 || lx == TILE) return (lx == TILE) * TILE1 * TILE1 + ly * TILE1 + lz;
-  if (ly == 0 || ly == TILE) return 2 * TILE1 * TILE1 + (ly == TILE) * (TILE - 1) * TILE1 + (lx - 1) * TILE1 + lz;
-  return 2 * TILE1 * TILE1 + 2 * (TILE - 1) * TILE1 + (lz == TILE) * (TILE - 1) * (TILE - 1) +
-         (lx - 1) * (TILE - 1) + (ly - 1);
-}
-
-__device__ __forceinline__ void shell_decode(int s, int* l) {
-  if (s < 2 * TILE1 * TILE1) {
-    l[0] = (s >= TILE1 * TILE1) ? TILE : 0;
-    s %= TILE1 * TILE1;
-    l[1] = s / TILE1;
-    l[2] = s % TILE1;
-    return;
-  }
-  s -= 2 * TILE1 * TILE1;
-  if (s < 2 * (TILE - 1) * TILE1) {
-    l[1] = (s >= (TILE - 1) * TILE1) ? TILE : 0;
-    s %= (TILE - 1) * TILE1;
-    l[0] = 1 + s / TILE1;
-    l[2] = s % TILE1;
-    return;
-  }
-  s -= 2 * (TILE - 1) * TILE1;
-  l[2] = (s >= (TILE - 1) * (TILE - 1)) ? TILE : 0;
-  s %= (TILE - 1) * (TILE - 1);
-  l[0] = 1 + s / (TILE - 1);
-  l[1] = 1 + s % (TILE - 1);
-}
-
-// Deposit one warp's particles.  When the warp holds long runs of the same
-// local cell in adjacent lanes, each run is summed first (segmented
-// shuffle reduction; a run of <= 32 weights of <= 2^24 fits 32 bits) and
-// its head lane adds the 8 corner sums; otherwise every lane adds its own.
-__device__ __forceinline__ void deposit_warp(uint32_t* lo, uint32_t* hi, bool active, const int* l,
-                                             const float* t) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  uint32_t w[8];
-  {
-    const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      w[c] = active ? __float2uint_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * W_ONE) : 0u;
-  }
-  const int key = active ? (l[0] * TILE + l[1]) * TILE + l[2] : -1 - lane;
-  const int prev = __shfl_up_sync(full, key, 1);
-  const bool head = (lane == 0) || (prev != key);
-  const unsigned heads = __ballot_sync(full, head);
-  const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
-  if (__popc(heads) > 24) {
-    if (active) {
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        acc_add(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
-    }
-    return;
-  }
-  const unsigned after = heads & ~((2u << lane) - 1u);
-  const int seg_end = after ? __ffs(after) - 1 : 32;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    uint32_t s = w[c];
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t o = __shfl_down_sync(full, s, off);
-      if (lane + off < seg_end) s += o;
-    }
-    w[c] = s;
-  }
-  if (active && head) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      acc_add(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
-  }
-}
-
-// Local cell (relative to tile origin o) and fraction of particle i.
-__device__ __forceinline__ bool particle_local(const float* __restrict__ dx, size_t N, uint32_t i,
-                                               const Geom& g, const int* o, int* l, float* t) {
-  int q[3], c[3];
-  lattice_node(i, g, q);
-  bool ok = true;
-  for (int d = 0; d < 3; ++d) ok &= cic_cell(__ldg(dx + d * N + i), q[d], g.nc, &c[d], &t[d]);
-  for (int d = 0; d < 3; ++d) {
-    l[d] = c[d] - o[d];
-    if (l[d] < 0 || l[d] >= TILE) {   // cannot happen for a consistent key; guard anyway
-      ok = false;
-      l[d] = 0;
-    }
-  }
-  return ok;
-}
-
-// Write the tile's interior cells (final) and its 17^3 shell (partials).
-__device__ __forceinline__ void paint_writeout(const uint32_t* lo, const uint32_t* hi, const int* o, int tile,
-                                               const Geom& g, float* __restrict__ rho,
-                                               unsigned long long* __restrict__ halo) {
-  const int nc = g.nc;
-  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
-    const int lx = 1 + k / ((TILE - 1) * (TILE - 1));
-    const int ly = 1 + (k / (TILE - 1)) % (TILE - 1);
-    const int lz = 1 + k % (TILE - 1);
-    rho[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
-        from_fix(acc_get(lo, hi, (lx * TILE1 + ly) * TILE1 + lz), g.mass);
-  }
-  unsigned long long* hb = halo + (size_t)tile * SHELL;
-  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
-    int l[3];
-    shell_decode(s, l);
-    hb[s] = acc_get(lo, hi, (l[0] * TILE1 + l[1]) * TILE1 + l[2]);
-  }
-}
-
-// Hot-path paint: one CTA per tile, particles in bucket order.
 __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,
                                                              const uint32_t* __restrict__ items,
                                                              const uint32_t* __restrict__ tile_start, Geom g,
@@ -302,25 +52,23 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __rest
                                                              unsigned long long* __restrict__ halo,
                                                              int* __restrict__ err) {
   __shared__ uint32_t lo[ACC], hi[ACC];
-  const int nt = g.nt;
-  const int tile = blockIdx.x;
-  const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
-  const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
-  const int n = (int)(s1 - s0);
-  for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
-  __syncthreads();
-  bool bad = false;
-  const int nw = (n + 31) & ~31;
-  for (int k = threadIdx.x; k < nw; k += blockDim.x) {
-    const bool active = k < n;
-    int l[3] = {0, 0, 0};
-    float t[3] = {0.f, 0.f, 0.f};
-    if (active) bad |= !particle_local(dx, N, __ldg(items + s0 + k), g, o, l, t);
-    deposit_warp(lo, hi, active, l, t);
-  }
-  if (bad) atomicOr(err, ERR_RANGE);
-  __syncthreads();
-  paint_writeout(lo, hi, o, tile, g, rho, halo);
+  body_paint_bucket(dx, N, items, tile_start, g, rho, halo, err, lo, hi, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(768) k_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
+                                                    float* __restrict__ rho) {
+  __shared__ uint32_t nb[8];
+  body_paint_halo(halo, g, rho, nb, blockIdx.x);
+}
+
+template <bool KDK, bool F4>
+__global__ void __launch_bounds__(256) k_readout(float* __restrict__ dx, float* __restrict__ p,
+                                                 const float* __restrict__ F, Geom g, size_t N, size_t M,
+                                                 const double* __restrict__ fac, int ik1, int ik2, int idr,
+                                                 float* __restrict__ f_out, uint32_t* __restrict__ keys,
+                                                 uint32_t* __restrict__ tile_count, int* __restrict__ err,
+                                                 int iters) {
+  body_readout<KDK, F4>(dx, p, F, g, N, M, fac, ik1, ik2, idr, f_out, keys, tile_count, err, iters, blockIdx.x);
 }
 
 // Paint with the permutation output: counting sort of the tile's bucket by
@@ -417,49 +165,6 @@ __global__ void __launch_bounds__(PS_THREADS) k_paint_sorted(const float* __rest
   paint_writeout(lo, hi, o, tile, g, rho, halo);
 }
 
-// Lower-face cells of every tile: sum the shell partials of the up to 8
-// tiles whose 17^3 blocks cover the cell.  One thread per face cell.
-__global__ void __launch_bounds__(768) k_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
-                                                    float* __restrict__ rho) {
-  __shared__ uint32_t nb[8];
-  const int nt = g.nt, nc = g.nc;
-  const int tile = blockIdx.x;
-  const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
-  if (threadIdx.x < 8) {
-    const int b = threadIdx.x;
-    const int x = tc[0] - (b >> 2), y = tc[1] - ((b >> 1) & 1), z = tc[2] - (b & 1);
-    nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
-  }
-  __syncthreads();
-  const int k = threadIdx.x;
-  if (k >= NFACE) return;
-  int l[3];
-  if (k < TILE * TILE) {
-    l[0] = 0;
-    l[1] = k >> 4;
-    l[2] = k & 15;
-  } else if (k < TILE * TILE + (TILE - 1) * TILE) {
-    const int r = k - TILE * TILE;
-    l[0] = 1 + (r >> 4);
-    l[1] = 0;
-    l[2] = r & 15;
-  } else {
-    const int r = k - TILE * TILE - (TILE - 1) * TILE;
-    l[0] = 1 + r / (TILE - 1);
-    l[1] = 1 + r % (TILE - 1);
-    l[2] = 0;
-  }
-  unsigned long long sum = 0;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
-    if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
-    sum += halo[(size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz)];
-  }
-  rho[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
-      from_fix(sum, g.mass);
-}
-
 // Stable order of one oversized tile for the permutation output: counting
 // sort by local cell with a global cursor table, then the index tie-fix.
 // One CTA per tile; tiles within PCAP return at once.
@@ -498,110 +203,6 @@ __global__ void k_perm_big(const uint32_t* __restrict__ items, const uint32_t* _
       }
       perm[b] = v;
     }
-  }
-}
-
-// ---------------------------------------------------------------- readout (+ kick, drift)
-// f_i = sum_c W(x_i - c) F_c.  With KDK: p += K f, dx += D p, then the new
-// cell key and tile histogram of the drifted particle.
-// Force at CIC corner `idx`: three separate meshes, or interleaved float4.
-template <bool F4>
-__device__ __forceinline__ void corner_force(const float* __restrict__ F, size_t M, size_t idx, float w,
-                                             float* f) {
-  if (F4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(F) + idx);
-    f[0] = fmaf(w, v.x, f[0]);
-    f[1] = fmaf(w, v.y, f[1]);
-    f[2] = fmaf(w, v.z, f[2]);
-  } else {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) f[a] = fmaf(w, __ldg(F + a * M + idx), f[a]);
-  }
-}
-
-template <bool KDK, bool F4>
-__global__ void __launch_bounds__(256) k_readout(float* __restrict__ dx, float* __restrict__ p,
-                                                 const float* __restrict__ F, Geom g, size_t N, size_t M,
-                                                 const double* __restrict__ fac, int ik1, int ik2, int idr,
-                                                 float* __restrict__ f_out, uint32_t* __restrict__ keys,
-                                                 uint32_t* __restrict__ tile_count, int* __restrict__ err,
-                                                 int iters) {
-  // each CTA walks a contiguous chunk of iters*256 particles, so that the
-  // force rows its neighbouring lattice rows share stay in its L1; the next
-  // chunk's dx and p are fetched while the current one gathers its forces
-  const int nc = g.nc;
-  float K = 0.f, D = 0.f;
-  if (KDK) {
-    K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
-    D = idr >= 0 ? (float)fac[idr] : 0.f;
-  }
-  const size_t c0 = (size_t)blockIdx.x * iters * blockDim.x;
-  float dn[3] = {0.f, 0.f, 0.f}, pn[3] = {0.f, 0.f, 0.f};
-  {
-    const size_t i = c0 + threadIdx.x;
-    if (i < N) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dn[a] = dx[a * N + i];
-        if (KDK) pn[a] = p[a * N + i];
-      }
-    }
-  }
-  for (int it = 0; it < iters; ++it) {
-    if (c0 + (size_t)it * blockDim.x >= N) break;
-    const size_t i = c0 + (size_t)it * blockDim.x + threadIdx.x;
-    const bool active = i < N;
-    float d[3] = {dn[0], dn[1], dn[2]}, pp[3] = {pn[0], pn[1], pn[2]};
-    const size_t inext = i + blockDim.x;
-    if (it + 1 < iters && inext < N) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dn[a] = dx[a * N + inext];
-        if (KDK) pn[a] = p[a * N + inext];
-      }
-    }
-    int tile = 0;
-    if (active) {
-      int q[3], c[3];
-      float t[3];
-      lattice_node((uint32_t)i, g, q);
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-      const int cx1 = (c[0] + 1 == nc) ? 0 : c[0] + 1;
-      const int cy1 = (c[1] + 1 == nc) ? 0 : c[1] + 1;
-      const int cz1 = (c[2] + 1 == nc) ? 0 : c[2] + 1;
-      const size_t rx[2] = {(size_t)c[0] * nc * nc, (size_t)cx1 * nc * nc};
-      const int ry[2] = {c[1] * nc, cy1 * nc};
-      const int rz[2] = {c[2], cz1};
-      const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
-      float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int b = 0; b < 8; ++b)
-        corner_force<F4>(F, M, rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1],
-                         wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1], f);
-      if (!KDK) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) f_out[a * N + i] = f[a];
-      } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float pa = fmaf(K, f[a], pp[a]);
-          p[a * N + i] = pa;
-          d[a] = fmaf(D, pa, d[a]);
-          dx[a * N + i] = d[a];
-        }
-        if (keys) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-          const uint32_t key = tile_key(c, g.nt);
-          keys[i] = key;
-          tile = key >> 12;
-        }
-      }
-      if (!ok) atomicOr(err, ERR_NAN);
-    }
-    if (KDK && keys) warp_count(tile_count, tile, active);
   }
 }
 
