@@ -48,6 +48,10 @@ def _alg_bytes(cls, N, M, nc):
         "fft_x_green": (h + 3 * h) * M / N,
         "fft_y_inv": 6 * h * M / N,
         "fft_z_c2r": (3 * h + 12) * M / N,
+        "pot_fft_fwd_zy": (4 + h) * M / N,           # rho read, half spectrum written once
+        "pot_fft_x_green": 2 * h * M / N,
+        "pot_fft_inv_yz": (h + 4) * M / N,           # half spectrum read, phi written once
+        "pot_gradient": (4 + 16) * M / N,            # phi read, float4 force mesh written
     }
     v = table.get(cls)
     return None if v is None else v * N

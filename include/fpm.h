@@ -261,7 +261,7 @@ int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream)
 #define FPM_K_SCATTER 3   /* bucketing of particles by tile                  */
 #define FPM_K_PAINT 4     /* in-tile counting sort + fixed-point CIC paint   */
 #define FPM_K_HALO 5      /* tile-face sums of the paint                     */
-#define FPM_K_FFT_ZF 6    /* z pass, real-to-complex                         */
+#define FPM_K_FFT_ZF 6    /* z pass, real-to-complex (other mesh sizes)      */
 #define FPM_K_FFT_YF 7    /* y pass, forward                                 */
 #define FPM_K_FFT_X 8     /* x pass with the Eq. 3-5 transfer function       */
 #define FPM_K_FFT_YI 9    /* y pass, inverse (3 fields)                      */
@@ -270,7 +270,12 @@ int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream)
 #define FPM_K_IC 12       /* linear field and 2LPT                           */
 #define FPM_K_COEF 13     /* FP64 growth and FastPM factors                  */
 #define FPM_K_POWER 14    /* power spectrum                                  */
-#define FPM_K_COUNT 15
+/* Power-of-two meshes compute the force through the potential (Eqs. 3-5):  */
+#define FPM_K_POT_FWD 15  /* z r2c + y forward, one slab-ordered launch      */
+#define FPM_K_POT_X 16    /* x pass with the Green's function (1 field)      */
+#define FPM_K_POT_INV 17  /* y inverse + z c2r to phi, one slab-ordered launch */
+#define FPM_K_POT_GRAD 18 /* Eq. 5 difference of phi to the force meshes     */
+#define FPM_K_COUNT 19
 
 /* Turn per-kernel-class timing on or off for this plan (off by default).
  * When on, every launch of the plan is bracketed by CUDA events recorded on

@@ -28,7 +28,7 @@ EXPORTS = [
     "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
     "fpm_batch_status", "fpm_batch_info",
 ]
-FPM_K_COUNT = 15
+FPM_K_COUNT = 19
 
 
 class FpmError(RuntimeError):

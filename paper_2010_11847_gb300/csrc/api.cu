@@ -47,6 +47,7 @@ struct fpm_plan {
   float* real6 = nullptr;      // 6 real lattice fields (2LPT Hessian)
   float* rho = nullptr;        // density mesh
   float* F = nullptr;          // 3 force meshes
+  unsigned* slab_ctr = nullptr;  // work counters of the slab-ordered FFT launches
   PaintCtx pc;
   double* d_amp = nullptr;     // P(k) amplitude (sigma8 normalisation)
   double* d_pts = nullptr;     // scale factors of a coefficient request
@@ -95,6 +96,7 @@ void free_plan(fpm_plan* p) {
   cudaFree(p->real6);
   cudaFree(p->rho);
   cudaFree(p->F);
+  cudaFree(p->slab_ctr);
   cudaFree(p->pc.keys);
   cudaFree(p->pc.items);
   cudaFree(p->pc.tile_count);
@@ -172,6 +174,18 @@ int timed(fpm_plan* p, int cls, int nk, cudaStream_t s, Fn fn) {
 int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s, bool interleaved = false) {
   const FftTables& t = p->tc;
   const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
+  if (fft_has_potential(t.n)) {
+    // phi = IFFT[coef delta / |w|^2] in the second half spectrum's memory,
+    // then F_d = D_d phi (the Eq. 5 difference) in real space
+    float* phi = reinterpret_cast<float*>(p->spec + p->specmax);
+    const int fused = t.n >= 128 ? 1 : 2;
+    FPM_TRY(timed(p, FPM_K_POT_FWD, fused, s,
+                  [&] { return fft_pot_forward(t, rho, p->spec, p->slab_ctr, p->d_err, s); }));
+    FPM_TRY(timed(p, FPM_K_POT_X, 1, s, [&] { return fft_pot_xgreen(t, p->spec, coef, s); }));
+    FPM_TRY(timed(p, FPM_K_POT_INV, fused, s,
+                  [&] { return fft_pot_inverse(t, p->spec, phi, p->slab_ctr, p->d_err, s); }));
+    return timed(p, FPM_K_POT_GRAD, 1, s, [&] { return fft_pot_gradient(t, phi, F, interleaved, p->M, s); });
+  }
   FPM_TRY(timed(p, FPM_K_FFT_ZF, 1, s, [&] { return fft_zfwd(t, rho, p->spec, 1, 0, 0, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_YF, 1, s, [&] { return fft_y(t, p->spec, 1, 0, false, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_X, 1, s, [&] { return fft_xforce(t, p->spec, p->spec, p->specmax, coef, s); }));
@@ -259,6 +273,7 @@ int fpm_plan_create(fpm_plan** out, int np, int nc, double box, const fpm_cosmo*
   TRY(dalloc(p, &p->real6, 6 * p->N));
   TRY(dalloc(p, &p->rho, p->M));
   TRY(dalloc(p, &p->F, 4 * p->M));
+  TRY(dalloc(p, &p->slab_ctr, (size_t)(1 + MAX_N)));
   p->f4 = fft_has_interleaved(nc);
   PaintCtx& c = p->pc;
   c.g = make_geom(np, nc);
@@ -461,7 +476,9 @@ const char* fpm_kernel_class_name(int cls) {
   static const char* names[FPM_K_COUNT] = {"kdk_readout_kick_drift", "cell_keys", "tile_scan", "tile_scatter",
                                            "paint_tiles", "paint_halo", "fft_z_r2c", "fft_y_fwd",
                                            "fft_x_green", "fft_y_inv", "fft_z_c2r", "readout",
-                                           "initial_conditions", "coefficients_fp64", "power_spectrum"};
+                                           "initial_conditions", "coefficients_fp64", "power_spectrum",
+                                           "pot_fft_fwd_zy", "pot_fft_x_green", "pot_fft_inv_yz",
+                                           "pot_gradient"};
   return (cls >= 0 && cls < FPM_K_COUNT) ? names[cls] : "unknown";
 }
 

@@ -4,10 +4,13 @@
 // Each simulation keeps its own plan (sizes, cosmology, FP64 kick/drift
 // factors, scratch).  A launch runs the phases of one step -- readout +
 // kick + drift + keys, tile scan, scatter, paint, halo, z/y/x/y/z FFT passes
-// with the force transfer function -- over a work list that spans every
+// to the potential and its finite-difference gradient (power-of-two meshes;
+// 96 keeps the three-field spectral gradient) -- over a work list that spans every
 // simulation: work item j of a phase is mapped to (simulation, local block)
 // through per-phase prefix offsets, and the body of the matching kernel runs
 // with that local block index, dispatching on the simulation's mesh size.
+// Data written earlier in the same launch is read L2-coherently (ld.cg),
+// never through the read-only path.
 // Phases are separated by a grid barrier whose wait is bounded: past the
 // spin limit the block records FPM_ETIMEOUT and stops, so a broken barrier
 // can end the run early but never hang the GPU.  A whole run (initial force,
@@ -26,7 +29,8 @@ constexpr int BT = 256;        // threads of the persistent kernel
 constexpr size_t BATCH_SMEM = 40 * 1024;
 
 enum Phase : int {
-  PH_KEYS = 0, PH_KDK, PH_SCAN, PH_SCATTER, PH_PAINT, PH_HALO, PH_ZF, PH_YF, PH_X, PH_YI, PH_ZI, PH_KDK_LAST, NPH
+  PH_KEYS = 0, PH_KDK, PH_SCAN, PH_SCATTER, PH_PAINT, PH_HALO, PH_ZF, PH_YF, PH_X, PH_YI, PH_ZI, PH_GRAD, PH_KDK_LAST,
+  NPH
 };
 
 struct SimDesc {
@@ -101,19 +105,27 @@ __device__ __forceinline__ int find_sim(const int* off, int nsims, int item) {
   return lo;
 }
 
+// Power-of-two meshes: the force through the potential, as in the
+// single-simulation path (same bodies, hence the same bits): phi in the
+// memory of the second half spectrum, then the Eq. 5 difference.
 template <int N>
 __device__ void fft_phase_pow2(int ph, const SimDesc& d, int local, float2* sm) {
-  using C = RegCfg<N>;
   const int nlines = (N / 2 + 1) * N;
-  const int per_field = (nlines + C::L - 1) / C::L;
+  float* phi = reinterpret_cast<float*>(d.spec + d.specmax);
   switch (ph) {
     case PH_ZF: body_zfwd_r<N>(d.rho, d.spec, 0, 0, d.tw, sm, local, 0); break;
     case PH_YF: body_yfft_r<N, false>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
-    case PH_X: body_xforce_r<N>(d.spec, d.spec, d.specmax, d.force_coef, d.tw, d.gk, d.w2, sm, local, 0); break;
-    case PH_YI:
-      body_yfft_r<N, true>(d.spec, nlines, d.specmax, d.tw, sm, local % per_field, local / per_field);
+    case PH_X: body_xgreen_r<N>(d.spec, d.force_coef, d.tw, d.w2, sm, local); break;
+    case PH_YI: body_yfft_r<N, true>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
+    case PH_ZI: body_zinv_r<N>(d.spec, phi, 0, 0, d.tw, sm, local, 0); break;
+    case PH_GRAD: {
+      using SC = StCfg<N>;
+      constexpr int nbz = N / SC::TZ, nby = N / SC::TY;
+      const int bz = local % nbz, by = (local / nbz) % nby, bx = local / (nbz * nby);
+      if (d.f4) body_stencil<N, true>(phi, d.F, d.M, reinterpret_cast<float*>(sm), bz, by, bx);
+      else body_stencil<N, false>(phi, d.F, d.M, reinterpret_cast<float*>(sm), bz, by, bx);
       break;
-    case PH_ZI: body_zinv3_r<N>(d.spec, reinterpret_cast<float4*>(d.F), d.specmax, d.tw, sm, local, 0); break;
+    }
     default: break;
   }
 }
@@ -138,13 +150,13 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   uint32_t* su = reinterpret_cast<uint32_t*>(smraw);
-  int phases[11];
+  int phases[12];
   int nph = 0;
   if (a.kind == 2) {
     phases[nph++] = PH_KDK_LAST;
   } else {
     phases[nph++] = a.kind == 0 ? PH_KEYS : PH_KDK;
-    for (int ph = PH_SCAN; ph <= PH_ZI; ++ph) phases[nph++] = ph;
+    for (int ph = PH_SCAN; ph <= PH_GRAD; ++ph) phases[nph++] = ph;
   }
   for (int q = 0; q < nph; ++q) {
     const int ph = phases[q];
@@ -164,16 +176,16 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
           const int idr = last ? -1 : 3 * k + 1;
           uint32_t* keys = last ? nullptr : d.keys;
           if (d.f4)
-            body_readout<true, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+            body_readout<true, true, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
                                      d.tile_count, d.err, a.ro_iters, local);
           else
-            body_readout<true, false>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+            body_readout<true, false, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
                                       d.tile_count, d.err, a.ro_iters, local);
           break;
         }
         case PH_SCAN: body_scan_tiles(d.tile_count, d.ntiles, d.tile_start, d.tile_cursor, su, 1); break;
         case PH_SCATTER: body_scatter(d.keys, d.N, d.tile_cursor, d.items, local); break;
-        case PH_PAINT: body_paint_bucket(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err, su,
+        case PH_PAINT: body_paint_bucket<true>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err, su,
                                          su + ACC, local); break;
         case PH_HALO: body_paint_halo(d.halo, d.g, d.rho, su, local); break;
         default:
@@ -210,17 +222,20 @@ static void items_for(SimDesc& d, int ro_iters) {
     default: break;
   }
   if (L) {
+    const int tz = nc < 32 ? nc : 32, ty = 256 / tz, xc = nc < ST_XC ? nc : ST_XC;
     d.items_of[PH_ZF] = nc * nc / (2 * L);
     d.items_of[PH_YF] = (nlines + L - 1) / L;
     d.items_of[PH_X] = (nlines + L - 1) / L;
-    d.items_of[PH_YI] = 3 * ((nlines + L - 1) / L);
+    d.items_of[PH_YI] = (nlines + L - 1) / L;
     d.items_of[PH_ZI] = nc * nc / (2 * L);
+    d.items_of[PH_GRAD] = (nc / tz) * (nc / ty) * (nc / xc);
   } else {   // 96 = 3 * 32: shared-memory Stockham passes
     d.items_of[PH_ZF] = nc * (nc / (2 * ZG));
     d.items_of[PH_YF] = (nlines + YL - 1) / YL;
     d.items_of[PH_X] = nh * (nc / XB);
     d.items_of[PH_YI] = 3 * ((nlines + YL - 1) / YL);
     d.items_of[PH_ZI] = 3 * nc * (nc / (2 * ZG));
+    d.items_of[PH_GRAD] = 0;
   }
 }
 

@@ -44,7 +44,7 @@ __device__ __forceinline__ void body_zfwd(const float* __restrict__ in, float2* 
   const float* src = in + by * in_fs + ((size_t)x * N + y0) * N;
   for (int idx = threadIdx.x; idx < ZG * N; idx += blockDim.x) {
     const int g = idx / N, z = idx - g * N;
-    a[g * LS + sp(z)] = make_float2(__ldg(src + (2 * g) * N + z), __ldg(src + (2 * g + 1) * N + z));
+    a[g * LS + sp(z)] = make_float2(__ldcg(src + (2 * g) * N + z), __ldcg(src + (2 * g + 1) * N + z));
   }
   __syncthreads();
   const float2* r = FftPlan<N>::template run<false>(a, b, ZG, LS, tw);
@@ -113,7 +113,7 @@ __device__ __forceinline__ void body_zinv(const float2* __restrict__ in, float* 
   const float4* src = reinterpret_cast<const float4*>(in + by * in_fs + (size_t)x * NH * N + y0);
   for (int idx = threadIdx.x; idx < NH * ZG; idx += blockDim.x) {
     const int kz = idx / ZG, g = idx - kz * ZG;
-    const float4 v = __ldg(src + ((size_t)kz * N) / 2 + g);   // A = (x, y), B = (z, w)
+    const float4 v = __ldcg(src + ((size_t)kz * N) / 2 + g);   // A = (x, y), B = (z, w)
     if (kz == 0 || kz == N / 2) {
       a[g * LS + sp(kz)] = make_float2(v.x, v.z);
     } else {
@@ -147,7 +147,7 @@ __device__ __forceinline__ void xload(float2* dst, const float2* __restrict__ sp
   constexpr size_t S = (size_t)(N / 2 + 1) * N;
   for (int idx = threadIdx.x; idx < N * XB; idx += blockDim.x) {
     const int x = idx / XB, j = idx - x * XB;
-    dst[j * LS + sp(x)] = __ldg(spec + x * S + (size_t)kz * N + ky0 + j);
+    dst[j * LS + sp(x)] = __ldcg(spec + x * S + (size_t)kz * N + ky0 + j);
   }
 }
 

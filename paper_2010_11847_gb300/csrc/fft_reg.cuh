@@ -12,6 +12,10 @@
 // pointwise operator and an inverse transform chain without touching memory.
 // N = 512 = 8*8*8 needs two exchanges; twiddles come from the host FP64
 // table staged in shared memory.
+//
+// Field data is loaded with ld.global.cg (L2, never the read-only path):
+// the same bodies run inside persistent launches where another block wrote
+// the data earlier in the launch.
 #pragma once
 #include "fft.cuh"
 #include "internal.h"
@@ -117,7 +121,7 @@ __device__ __forceinline__ void body_zfwd_r(const float* __restrict__ in,
   const float* src = in + by * in_fs + (r0 + 2 * g) * N;
   float2 v[8];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = make_float2(__ldg(src + t + T * s), __ldg(src + N + t + T * s));
+  for (int s = 0; s < 8; ++s) v[s] = make_float2(__ldcg(src + t + T * s), __ldcg(src + N + t + T * s));
   __syncthreads();
   float2* buf = xb + g * rline<N>();
   RegFft<N>::template run<false>(v, buf, t, tw);
@@ -161,7 +165,7 @@ __device__ __forceinline__ void body_yfft_r(float2* __restrict__ data, int nline
   float2* base = data + by * fs + (size_t)gl * N;
   float2 v[8];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = valid ? base[t + T * s] : make_float2(0.f, 0.f);
+  for (int s = 0; s < 8; ++s) v[s] = valid ? __ldcg(base + t + T * s) : make_float2(0.f, 0.f);
   __syncthreads();
   RegFft<N>::template run<INV>(v, xb + line * rline<N>(), t, tw);
   if (valid) {
@@ -193,7 +197,7 @@ __device__ __forceinline__ void body_zinv_r(const float2* __restrict__ in,
     const int kz = idx / L, gg = idx - kz * L;
     const size_t row = r0 + 2 * gg;
     const size_t x = row / N, y = row - x * N;
-    const float4 v = __ldg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
     float2* b = xb + gg * rline<N>();
     if (kz == 0 || kz == N / 2) {
       b[rp(kz)] = make_float2(v.x, v.z);
@@ -247,7 +251,7 @@ __device__ __forceinline__ void body_zinv3_r(const float2* __restrict__ in, floa
       const int kz = idx / L, gg = idx - kz * L;
       const size_t row = r0 + 2 * gg;
       const size_t x = row / N, y = row - x * N;
-      const float4 v = __ldg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(src + (x * NH + kz) * N + y));
       float2* b = xb + gg * rline<N>();
       if (kz == 0 || kz == N / 2) {
         b[rp(kz)] = make_float2(v.x, v.z);
@@ -298,7 +302,7 @@ __device__ __forceinline__ void body_xforce_r(const float2* in, float2* out, siz
   const int kz = gl / N, ky = gl - kz * N;
   float2 d[8];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) d[s] = valid ? in[(size_t)(t + T * s) * S + gl] : make_float2(0.f, 0.f);
+  for (int s = 0; s < 8; ++s) d[s] = valid ? __ldcg(in + (size_t)(t + T * s) * S + gl) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* buf = xb + line * rline<N>();
   RegFft<N>::template run<false>(d, buf, t, tw);
@@ -325,6 +329,130 @@ __device__ __forceinline__ void body_xforce_r(const float2* in, float2* out, siz
       for (int s = 0; s < 8; ++s) o[(size_t)(t + T * s) * S + gl] = v[s];
     }
   }
+}
+
+// ---------------------------------------------------------------- x pass: potential
+// One field in place: forward x transform of delta(k), the Green's function
+// phi = coef delta / |w|^2 (0 at k = 0, Eq. 3), inverse x transform.  The
+// Eq. 5 finite-difference gradient is then applied in real space to phi.
+template <int N>
+__device__ __forceinline__ void body_xgreen_r(float2* data, float coef, const float2* __restrict__ g_tw,
+                                              const float* __restrict__ g_w2, float2* smem, int bx) {
+  using C = RegCfg<N>;
+  constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
+  constexpr size_t S = (size_t)NH * N;
+  float2* tw = smem;
+  float2* xb = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
+  const int line = threadIdx.x % L, t = threadIdx.x / L;
+  const int gl = bx * L + line;
+  const bool valid = gl < NH * N;
+  const int kz = gl / N, ky = gl - kz * N;
+  float2 d[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) d[s] = valid ? __ldcg(data + (size_t)(t + T * s) * S + gl) : make_float2(0.f, 0.f);
+  __syncthreads();
+  float2* buf = xb + line * rline<N>();
+  RegFft<N>::template run<false>(d, buf, t, tw);
+  const float w2yz = valid ? __ldg(g_w2 + ky) + __ldg(g_w2 + kz) : 1.f;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const float k2 = __ldg(g_w2 + t + T * s) + w2yz;
+    d[s] = cscale(d[s], k2 > 0.f ? coef / k2 : 0.f);
+  }
+  RegFft<N>::template run<true>(d, buf, t, tw);
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) data[(size_t)(t + T * s) * S + gl] = d[s];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_xgreen_r(float2* data, float coef,
+                                                                 const float2* __restrict__ g_tw,
+                                                                 const float* __restrict__ g_w2) {
+  extern __shared__ float2 smem[];
+  body_xgreen_r<N>(data, coef, g_tw, g_w2, smem, blockIdx.x);
+}
+
+// ---------------------------------------------------------------- real-space gradient
+// F_d(c) = [8 (phi(c + e_d) - phi(c - e_d)) - (phi(c + 2 e_d) - phi(c - 2 e_d))] / 12,
+// whose Fourier symbol is i (8 sin w - sin 2w) / 6 = i g(w) of Eq. 5 (zero
+// at the Nyquist frequency by itself).  A block owns a TZ x TY patch of a
+// y-z plane and marches through XC planes of x, keeping a ring of five
+// halo-padded planes in shared memory; the next plane is fetched into
+// registers while the current one is differenced.
+constexpr int ST_XC = 32;                  // x planes per block
+template <int N>
+struct StCfg {
+  static constexpr int TZ = N < 32 ? N : 32;
+  static constexpr int TY = 256 / TZ;
+  static constexpr int PZ = TZ + 4, PY = TY + 4, PLANE = PZ * PY;
+  static constexpr int XC = N < ST_XC ? N : ST_XC;
+  static constexpr int LOADS = (PLANE + 255) / 256;
+};
+
+__device__ __forceinline__ float fd4(float m2, float m1, float p1, float p2) {
+  return fmaf(0.6666666666666666f, p1 - m1, -0.08333333333333333f * (p2 - m2));
+}
+
+template <int N, bool F4>
+__device__ __forceinline__ void body_stencil(const float* __restrict__ phi, float* __restrict__ F, size_t M,
+                                             float* ring, int bz, int by, int bx) {
+  using C = StCfg<N>;
+  constexpr int TZ = C::TZ, TY = C::TY, PZ = C::PZ, PLANE = C::PLANE, XC = C::XC;
+  const int z0 = bz * TZ, y0 = by * TY, x0 = bx * XC;
+  const int tz = threadIdx.x % TZ, ty = threadIdx.x / TZ;
+  float pre[C::LOADS];
+  auto fetch = [&](int x) {
+    const float* pl = phi + (size_t)(x & (N - 1)) * N * N;
+#pragma unroll
+    for (int k = 0; k < C::LOADS; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      if (e < PLANE) {
+        const int r = e / PZ, c = e - r * PZ;
+        pre[k] = __ldcg(pl + (size_t)((y0 - 2 + r) & (N - 1)) * N + ((z0 - 2 + c) & (N - 1)));
+      }
+    }
+  };
+  auto stash = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < C::LOADS; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      if (e < PLANE) ring[slot * PLANE + e] = pre[k];
+    }
+  };
+  for (int j = 0; j < 4; ++j) {            // planes x0-2 .. x0+1
+    fetch(x0 - 2 + j);
+    stash(j);
+  }
+  fetch(x0 + 2);
+  const int cidx = (ty + 2) * PZ + tz + 2;
+  for (int j = 0; j < XC; ++j) {
+    stash((j + 4) % 5);
+    __syncthreads();
+    if (j + 1 < XC) fetch(x0 + j + 3);
+    const float* c = ring + ((j + 2) % 5) * PLANE;
+    const float fx = fd4(ring[(j % 5) * PLANE + cidx], ring[((j + 1) % 5) * PLANE + cidx],
+                         ring[((j + 3) % 5) * PLANE + cidx], ring[((j + 4) % 5) * PLANE + cidx]);
+    const float fy = fd4(c[cidx - 2 * PZ], c[cidx - PZ], c[cidx + PZ], c[cidx + 2 * PZ]);
+    const float fz = fd4(c[cidx - 2], c[cidx - 1], c[cidx + 1], c[cidx + 2]);
+    const size_t o = ((size_t)(x0 + j) * N + (y0 + ty)) * N + z0 + tz;
+    if (F4) {
+      reinterpret_cast<float4*>(F)[o] = make_float4(fx, fy, fz, 0.f);
+    } else {
+      F[o] = fx;
+      F[M + o] = fy;
+      F[2 * M + o] = fz;
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, bool F4>
+__global__ void __launch_bounds__(256) k_stencil(const float* __restrict__ phi, float* __restrict__ F, size_t M) {
+  __shared__ float ring[5 * StCfg<N>::PLANE];
+  body_stencil<N, F4>(phi, F, M, ring, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int N>

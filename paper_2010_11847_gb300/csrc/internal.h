@@ -56,6 +56,16 @@ int fft_xforce(const FftTables& t, const float2* in, float2* out, size_t out_fs,
 bool fft_has_interleaved(int n);
 int fft_zinv3(const FftTables& t, const float2* spec, float4* out, size_t in_fs, cudaStream_t s);
 
+// fft_slab.cu: the force through the potential, power-of-two meshes.
+// ctr: 1 + n words of device scratch (zeroed by the calls); err: device flag.
+bool fft_has_potential(int n);
+int fft_slab_planes(int n);
+int fft_pot_forward(const FftTables& t, const float* rho, float2* spec, unsigned* ctr, int* err, cudaStream_t s);
+int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, cudaStream_t s);
+int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr, int* err, cudaStream_t s);
+// F: interleaved float4 per cell (f4) or [3][M].
+int fft_pot_gradient(const FftTables& t, const float* phi, float* F, bool f4, size_t M, cudaStream_t s);
+
 // ic.cu
 int fft_xlinear(const FftTables& t, const float2* in, float2* out, const EhParams& e, const double* d_amp,
                 float kf, float n3v, cudaStream_t s);

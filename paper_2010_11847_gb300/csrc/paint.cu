@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_paint_sorted(const float* __rest
       const bool active = k < n;
       int l[3] = {0, 0, 0};
       float t[3] = {0.f, 0.f, 0.f};
-      if (active) bad |= !particle_local(dx, N, sorted[k], g, o, l, t);
+      if (active) bad |= !particle_local<false>(dx, N, sorted[k], g, o, l, t);
       deposit_warp(lo, hi, active, l, t);
     }
   } else {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_paint_sorted(const float* __rest
       const bool active = k < n;
       int l[3] = {0, 0, 0};
       float t[3] = {0.f, 0.f, 0.f};
-      if (active) bad |= !particle_local(dx, N, items[s0 + k], g, o, l, t);
+      if (active) bad |= !particle_local<false>(dx, N, items[s0 + k], g, o, l, t);
       deposit_warp(lo, hi, active, l, t);
     }
   }
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
     const uint32_t i = __ldg(items + k);
     int l[3];
     float t[3];
-    if (!particle_local(dx, N, i, g, o, l, t)) continue;
+    if (!particle_local<false>(dx, N, i, g, o, l, t)) continue;
     const float vs = __ldg(vch + i) * scale;
     const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};

@@ -150,7 +150,7 @@ __device__ __forceinline__ void body_scatter(const uint32_t* __restrict__ keys, 
 #pragma unroll
   for (int e = 0; e < SCAT_E; ++e) {
     const size_t i = i0 + (size_t)e * blockDim.x;
-    tile[e] = i < N ? (int)(__ldg(keys + i) >> 12) : -1 - lane;
+    tile[e] = i < N ? (int)(__ldcg(keys + i) >> 12) : -1 - lane;
     grp[e] = __match_any_sync(full, tile[e]);
   }
 #pragma unroll
@@ -261,13 +261,22 @@ __device__ __forceinline__ void deposit_warp(uint32_t* lo, uint32_t* hi, bool ac
   }
 }
 
+// Load of particle data: through the read-only path (COH = false), or
+// L2-coherent when another block of the same launch wrote it (COH = true).
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_part(const T* p) {
+  if (COH) return __ldcg(p);
+  return __ldg(p);
+}
+
 // Local cell (relative to tile origin o) and fraction of particle i.
+template <bool COH>
 __device__ __forceinline__ bool particle_local(const float* __restrict__ dx, size_t N, uint32_t i,
                                                const Geom& g, const int* o, int* l, float* t) {
   int q[3], c[3];
   lattice_node(i, g, q);
   bool ok = true;
-  for (int d = 0; d < 3; ++d) ok &= cic_cell(__ldg(dx + d * N + i), q[d], g.nc, &c[d], &t[d]);
+  for (int d = 0; d < 3; ++d) ok &= cic_cell(ld_part<COH>(dx + d * N + i), q[d], g.nc, &c[d], &t[d]);
   for (int d = 0; d < 3; ++d) {
     l[d] = c[d] - o[d];
     if (l[d] < 0 || l[d] >= TILE) {   // cannot happen for a consistent key; guard anyway
@@ -299,6 +308,7 @@ __device__ __forceinline__ void paint_writeout(const uint32_t* lo, const uint32_
 }
 
 // Hot-path paint: one CTA per tile, particles in bucket order.
+template <bool COH = false>
 __device__ __forceinline__ void body_paint_bucket(const float* __restrict__ dx, size_t N,
                                                              const uint32_t* __restrict__ items,
                                                              const uint32_t* __restrict__ tile_start, Geom g,
@@ -319,7 +329,7 @@ __device__ __forceinline__ void body_paint_bucket(const float* __restrict__ dx, 
     const bool active = k < n;
     int l[3] = {0, 0, 0};
     float t[3] = {0.f, 0.f, 0.f};
-    if (active) bad |= !particle_local(dx, N, __ldg(items + s0 + k), g, o, l, t);
+    if (active) bad |= !particle_local<COH>(dx, N, ld_part<COH>(items + s0 + k), g, o, l, t);
     deposit_warp(lo, hi, active, l, t);
   }
   if (bad) atomicOr(err, ERR_RANGE);
@@ -374,21 +384,21 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
 // f_i = sum_c W(x_i - c) F_c.  With KDK: p += K f, dx += D p, then the new
 // cell key and tile histogram of the drifted particle.
 // Force at CIC corner `idx`: three separate meshes, or interleaved float4.
-template <bool F4>
+template <bool F4, bool COH>
 __device__ __forceinline__ void corner_force(const float* __restrict__ F, size_t M, size_t idx, float w,
                                              float* f) {
   if (F4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(F) + idx);
+    const float4 v = ld_part<COH>(reinterpret_cast<const float4*>(F) + idx);
     f[0] = fmaf(w, v.x, f[0]);
     f[1] = fmaf(w, v.y, f[1]);
     f[2] = fmaf(w, v.z, f[2]);
   } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) f[a] = fmaf(w, __ldg(F + a * M + idx), f[a]);
+    for (int a = 0; a < 3; ++a) f[a] = fmaf(w, ld_part<COH>(F + a * M + idx), f[a]);
   }
 }
 
-template <bool KDK, bool F4>
+template <bool KDK, bool F4, bool COH = false>
 __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __restrict__ p,
                                                  const float* __restrict__ F, Geom g, size_t N, size_t M,
                                                  const double* __restrict__ fac, int ik1, int ik2, int idr,
@@ -447,7 +457,7 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
       float f[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int b = 0; b < 8; ++b)
-        corner_force<F4>(F, M, rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1],
+        corner_force<F4, COH>(F, M, rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1],
                          wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1], f);
       if (!KDK) {
 #pragma unroll

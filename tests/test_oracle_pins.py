@@ -326,6 +326,27 @@ def test_force_matches_brute_force_dft():
     np.testing.assert_allclose(F.reshape(3, -1), out, atol=1e-13)
 
 
+def test_force_is_four_point_difference_of_potential():
+    """Eq. 5's g(w) = (8 sin w - sin 2w)/6 is the symbol of the real-space
+    difference [8 (f(x+1) - f(x-1)) - (f(x+2) - f(x-2))] / 12, so the force
+    equals that stencil applied to phi = IFFT(1.5 Om delta / |w|^2) on each
+    axis (the form the CUDA path evaluates); Nyquist needs no special case."""
+    n = 12
+    delta = inputs.random_field(n, 23).astype(np.float64)
+    k = 2 * math.pi * np.fft.fftfreq(n)
+    kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    k2[0, 0, 0] = 1.0
+    dk = np.fft.fftn(delta) / k2
+    dk[0, 0, 0] = 0.0
+    phi = np.fft.ifftn(1.5 * OM * dk).real
+    F = O.force_from_delta(delta, OM)
+    for d in range(3):
+        r = lambda s: np.roll(phi, -s, axis=d)        # r(s)[x] = phi[x + s]
+        stencil = (8 * (r(1) - r(-1)) - (r(2) - r(-2))) / 12
+        np.testing.assert_allclose(F[d], stencil, atol=1e-13)
+
+
 def _ewald_force(r, L, m, om, alpha=None):
     """Periodic point-mass acceleration at displacement r from the source,
     for lap phi = 1.5 Om (rho - mean), by Ewald summation."""
