@@ -181,7 +181,7 @@ int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s, bool int
     const int fused = t.n >= 128 ? 1 : 2;
     FPM_TRY(timed(p, FPM_K_POT_FWD, fused, s,
                   [&] { return fft_pot_forward(t, rho, p->spec, p->slab_ctr, p->d_err, s); }));
-    FPM_TRY(timed(p, FPM_K_POT_X, 1, s, [&] { return fft_pot_xgreen(t, p->spec, coef, s); }));
+    FPM_TRY(timed(p, FPM_K_POT_X, 1, s, [&] { return fft_pot_xgreen(t, p->spec, coef, p->slab_ctr, p->d_err, s); }));
     FPM_TRY(timed(p, FPM_K_POT_INV, fused, s,
                   [&] { return fft_pot_inverse(t, p->spec, phi, p->slab_ctr, p->d_err, s); }));
     return timed(p, FPM_K_POT_GRAD, 1, s, [&] { return fft_pot_gradient(t, phi, F, interleaved, p->M, s); });

@@ -23,11 +23,33 @@
 namespace fpm {
 
 __device__ __forceinline__ int rp(int i) { return i + (i >> 3); }   // padded exchange index
+// Exchange index of a line: padded (LAY 0, line stride rline), or XOR-swizzled
+// within 16-element rows (LAY 1, line stride N + 2).  The swizzle makes both
+// the Stockham writes and the contiguous read-back free of bank conflicts
+// when a line's threads are consecutive lanes; the padding suits lines that
+// are interleaved across lanes (the x pass).
+__device__ __forceinline__ int sw16(int i) { return i ^ (((i >> 4) & 7) | ((i >> 3) & 8)); }
+template <int LAY>
+__device__ __forceinline__ int xidx(int i) { return LAY == 0 ? rp(i) : sw16(i); }
 template <int N>
 __host__ __device__ constexpr int rline() { return N + N / 8 + 1; }   // odd: lines start on distinct banks
 
-template <int N, int R, int NS, bool INV, bool LAST>
-__device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, const float2* tw) {
+// Barrier between exchange steps: the whole block (sid < 0), or only the
+// threads of one line -- named barrier sid for lines of >= 64 threads, the
+// warp for shorter lines.
+template <int T>
+__device__ __forceinline__ void xsync(int sid) {
+  if (sid < 0) {
+    __syncthreads();
+  } else if (T >= 64) {
+    asm volatile("bar.sync %0, %1;" ::"r"(sid), "n"(T) : "memory");
+  } else {
+    __syncwarp();
+  }
+}
+
+template <int N, int R, int NS, bool INV, bool LAST, int LAY>
+__device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, const float2* tw, int sid) {
   constexpr int T = N / 8, Q = 8 / R, TWS = N / (NS * R);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -51,28 +73,28 @@ __device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, co
     } else {
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[rp(base + r * NS)] = x[r];
+      for (int r = 0; r < R; ++r) buf[xidx<LAY>(base + r * NS)] = x[r];
     }
   }
   if (!LAST) {
-    __syncthreads();
+    xsync<T>(sid);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) v[s] = buf[rp(t + T * s)];
-    __syncthreads();
+    for (int s = 0; s < 8; ++s) v[s] = buf[xidx<LAY>(t + T * s)];
+    xsync<T>(sid);
   }
 }
 
-template <int N, bool INV, int NS, int... Rs>
+template <int N, bool INV, int LAY, int NS, int... Rs>
 struct RegStages;
-template <int N, bool INV, int NS>
-struct RegStages<N, INV, NS> {
-  static __device__ __forceinline__ void run(float2 (&)[8], float2*, int, const float2*) {}
+template <int N, bool INV, int LAY, int NS>
+struct RegStages<N, INV, LAY, NS> {
+  static __device__ __forceinline__ void run(float2 (&)[8], float2*, int, const float2*, int) {}
 };
-template <int N, bool INV, int NS, int R, int... Rs>
-struct RegStages<N, INV, NS, R, Rs...> {
-  static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw) {
-    reg_stage<N, R, NS, INV, sizeof...(Rs) == 0>(v, buf, t, tw);
-    RegStages<N, INV, NS * R, Rs...>::run(v, buf, t, tw);
+template <int N, bool INV, int LAY, int NS, int R, int... Rs>
+struct RegStages<N, INV, LAY, NS, R, Rs...> {
+  static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw, int sid) {
+    reg_stage<N, R, NS, INV, sizeof...(Rs) == 0, LAY>(v, buf, t, tw, sid);
+    RegStages<N, INV, LAY, NS * R, Rs...>::run(v, buf, t, tw, sid);
   }
 };
 
@@ -81,9 +103,10 @@ struct RegFft;
 #define FPM_REG_PLAN(NN, ...)                                                                  \
   template <>                                                                                  \
   struct RegFft<NN> {                                                                          \
-    template <bool INV>                                                                        \
-    static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw) { \
-      RegStages<NN, INV, 1, __VA_ARGS__>::run(v, buf, t, tw);                                  \
+    template <bool INV, int LAY = 0>                                                           \
+    static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw, \
+                                               int sid = -1) {                                 \
+      RegStages<NN, INV, LAY, 1, __VA_ARGS__>::run(v, buf, t, tw, sid);                        \
     }                                                                                          \
   };
 FPM_REG_PLAN(16, 8, 2)

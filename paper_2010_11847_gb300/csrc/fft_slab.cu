@@ -18,24 +18,32 @@
 // they are dead.
 //
 // Blocks claim items from a global counter in order, so an item only ever
-// waits on items claimed before it by running blocks: the launch needs no
-// co-residency guarantee and cannot deadlock.  A wait that runs past the
+// waits on items claimed before it by running blocks.  A block claims and
+// prefetches its next item while it transforms the current one (the
+// pipelined engine of fft_pipe.cuh); a second-phase item whose slab is not
+// finished yet is fetched only after the current item is done, so no block
+// waits while it holds an unfinished item: the launch needs no co-residency
+// guarantee and cannot deadlock.  The x pass runs on the same engine
+// without dependencies.  A wait that runs past the
 // spin limit records ERR_TIMEOUT and proceeds (results are then invalid and
 // fpm_status reports FPM_ETIMEOUT); once the flag is up no block waits again.
 #include "internal.h"
-#include "fft_reg.cuh"
+#include "fft_pipe.cuh"
 
 namespace fpm {
 
-struct SlabArgs {
+struct PipeArgs {
   const float* rho;     // forward: real mesh
   float2* spec;         // half spectrum [x][kz][y]
   float* phi;           // inverse: real potential
   const float2* tw;
+  const float* w2;
+  float coef;
   unsigned* ctr;        // [0] item counter, [1 + s] finished first-phase items of slab s
   int* err;
   int S;                // x planes per slab
-  long long spin_limit;
+  int D;                // lag of second-phase items, in slabs (1 <= D <= N / S)
+  long long wait_ns;     // limit of one dependency wait
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -44,49 +52,57 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, long long limit, int* err) {
-  long long spins = 0;
+// Bounded by time (%globaltimer): a profiler that slows the producers down
+// does not turn a normal wait into a reported timeout.
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, long long limit_ns, int* err) {
+  const unsigned long long t0 = gtimer_ns();
   while (ld_acquire_u32(c) < target) {
-    if ((*(volatile int*)err & ERR_TIMEOUT) || ++spins > limit) {
+    if ((*(volatile int*)err & ERR_TIMEOUT) || (long long)(gtimer_ns() - t0) > limit_ns) {
       atomicOr(err, ERR_TIMEOUT);
       return;
     }
-    __nanosleep(32);
+    __nanosleep(64);
   }
 }
 
-// Item order: A(0), then for k = 1 .. ns-1: A(k), B(k-1); then B(ns-1).
-__device__ __forceinline__ void slab_item(int item, int ns, int nA, int nB, int* ph, int* s, int* j) {
-  if (item < nA) {
-    *ph = 0; *s = 0; *j = item;
+// Item order with a lag of D slabs: A(0) .. A(D-1), then for k = D .. ns-1:
+// A(k), B(k-D); then B(ns-D) .. B(ns-1).  D is chosen so that a slab's
+// first-phase items are normally finished when its second-phase items are
+// claimed (every block holds up to two items in flight).
+__device__ __forceinline__ void slab_item(int item, int ns, int D, int nA, int nB, int* ph, int* s, int* j) {
+  const int head = D * nA, per = nA + nB;
+  if (item < head) {
+    *ph = 0; *s = item / nA; *j = item - (item / nA) * nA;
     return;
   }
-  const int r0 = item - nA, per = nA + nB;
-  const int k = 1 + r0 / per, r = r0 - (k - 1) * per;
-  if (k < ns && r < nA) {
-    *ph = 0; *s = k; *j = r;
-  } else if (k < ns) {
-    *ph = 1; *s = k - 1; *j = r - nA;
-  } else {
-    *ph = 1; *s = ns - 1; *j = r;
+  const int r0 = item - head;
+  const int k = D + r0 / per;
+  if (k < ns) {
+    const int r = r0 - (k - D) * per;
+    if (r < nA) {
+      *ph = 0; *s = k; *j = r;
+    } else {
+      *ph = 1; *s = k - D; *j = r - nA;
+    }
+    return;
   }
+  const int r1 = r0 - (ns - D) * per;
+  *ph = 1; *s = ns - D + r1 / nB; *j = r1 - (r1 / nB) * nB;
 }
-
-template <int N>
-struct SlabShape {
-  using C = RegCfg<N>;
-  static constexpr int NH = N / 2 + 1;
-  static constexpr int ZI = N / (2 * C::L);                 // z items per plane
-  static __host__ __device__ int y_items(int S) { return (S * NH + C::L - 1) / C::L; }
-};
 
 // Drop the 128-byte lines of the half spectrum that z item bx has read.
 template <int N>
 __device__ __forceinline__ void discard_z_item(const float2* spec, int bx) {
-  using C = RegCfg<N>;
-  constexpr int NH = N / 2 + 1, LPR = (2 * C::L * 8) / 128;
-  static_assert((2 * C::L * 8) % 128 == 0, "z item rows must cover whole lines");
-  const size_t r0 = (size_t)bx * 2 * C::L;
+  using P = PipeCfg<N>;
+  constexpr int NH = P::NH, LPR = (2 * P::L * 8) / 128;
+  static_assert((2 * P::L * 8) % 128 == 0, "z item rows must cover whole lines");
+  const size_t r0 = (size_t)bx * 2 * P::L;
   const size_t x = r0 / N, y0 = r0 - x * N;
   for (int e = threadIdx.x; e < NH * LPR; e += blockDim.x) {
     const int kz = e / LPR, l = e - kz * LPR;
@@ -95,46 +111,128 @@ __device__ __forceinline__ void discard_z_item(const float2* spec, int bx) {
   }
 }
 
-template <int N, bool INV>
-__global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS) k_slab(SlabArgs a) {
-  extern __shared__ float2 smem[];
-  __shared__ int s_item;
-  using SH = SlabShape<N>;
-  constexpr int NH = SH::NH, ZI = SH::ZI;
-  const int S = a.S, ns = N / S;
-  const int nA = INV ? SH::y_items(S) : S * ZI;
-  const int nB = INV ? S * ZI : SH::y_items(S);
-  const int total = ns * (nA + nB);
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.ctr, 1u);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= total) break;
-    int ph, s, j;
-    slab_item(item, ns, nA, nB, &ph, &s, &j);
-    float2* slab = a.spec + (size_t)s * S * NH * N;
-    if (ph == 0) {
-      if (INV) body_yfft_r<N, true>(slab, S * NH, 0, a.tw, smem, j, 0);
-      else body_zfwd_r<N>(a.rho, a.spec, 0, 0, a.tw, smem, s * S * ZI + j, 0);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(a.ctr + 1 + s, 1u);
-      }
+enum PipeKind : int { PK_FWD = 0, PK_INV = 1, PK_X = 2 };
+
+// KIND PK_FWD: A = z r2c (ZF), B = y forward; PK_INV: A = y inverse, B = z
+// c2r to phi (ZI); PK_X: x items only, no dependencies.
+template <int N, int KIND>
+struct PipeSched {
+  using P = PipeCfg<N>;
+  int S, ns, D, nA, nB, total;
+  __device__ PipeSched(int S_, int D_) : S(S_), ns(N / S_), D(D_) {
+    const int ny = (S * P::NH + P::L - 1) / P::L, nz = S * P::ZI;
+    if (KIND == PK_X) {
+      nA = P::NH * N / P::L;
+      nB = 0;
+      ns = 1;
+      D = 1;
     } else {
-      if (threadIdx.x == 0) wait_count(a.ctr + 1 + s, (unsigned)nA, a.spin_limit, a.err);
-      __syncthreads();
-      if (INV) {
-        const int bx = s * S * ZI + j;
-        body_zinv_r<N>(a.spec, a.phi, 0, 0, a.tw, smem, bx, 0);
-        __syncthreads();
-        discard_z_item<N>(a.spec, bx);
-      } else {
-        body_yfft_r<N, false>(slab, S * NH, 0, a.tw, smem, j, 0);
-      }
+      nA = KIND == PK_FWD ? nz : ny;
+      nB = KIND == PK_FWD ? ny : nz;
+    }
+    total = ns * (nA + nB);
+  }
+  __device__ void decode(int item, int* ph, int* s, int* j) const {
+    if (KIND == PK_X) {
+      *ph = 0; *s = 0; *j = item;
+    } else {
+      slab_item(item, ns, D, nA, nB, ph, s, j);
     }
   }
+};
+
+template <int N, int KIND>
+__device__ __forceinline__ void pipe_issue(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item, float2* buf) {
+  using P = PipeCfg<N>;
+  int ph, s, j;
+  sc.decode(item, &ph, &s, &j);
+  float2* slab = a.spec + (size_t)s * sc.S * P::NH * N;
+  const bool zitem = (KIND == PK_FWD && ph == 0) || (KIND == PK_INV && ph == 1);
+  if (KIND == PK_X) issue_x<N>(a.spec, j * P::L, buf);
+  else if (zitem && KIND == PK_FWD) issue_zf<N>(a.rho, (size_t)(s * sc.S * P::ZI + j) * 2 * P::L, buf);
+  else if (zitem) issue_zi<N>(a.spec, (size_t)(s * sc.S * P::ZI + j) * 2 * P::L, buf);
+  else issue_y<N>(slab, j * P::L, sc.S * P::NH, buf);
+}
+
+template <int N, int KIND>
+__device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item,
+                                             float2* buf, const float2* tw) {
+  using P = PipeCfg<N>;
+  int ph, s, j;
+  sc.decode(item, &ph, &s, &j);
+  float2* slab = a.spec + (size_t)s * sc.S * P::NH * N;
+  const int bx = s * sc.S * P::ZI + j;
+  if (KIND == PK_X) {
+    comp_x<N>(a.spec, j * P::L, a.coef, buf, tw, a.w2);
+  } else if (KIND == PK_FWD) {
+    if (ph == 0) comp_zf<N>(a.spec, (size_t)bx * 2 * P::L, buf, tw);
+    else comp_y<N, false>(slab, j * P::L, sc.S * P::NH, buf, tw);
+  } else {
+    if (ph == 0) comp_y<N, true>(slab, j * P::L, sc.S * P::NH, buf, tw);
+    else comp_zi<N>(a.phi, (size_t)bx * 2 * P::L, buf, tw);
+  }
+  if (KIND != PK_X && ph == 0) {            // publish a finished first-phase item
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.ctr + 1 + s, 1u);
+    }
+  }
+  if (KIND == PK_INV && ph == 1) discard_z_item<N>(a.spec, bx);
+}
+
+template <int N, int KIND>
+__global__ void __launch_bounds__(PipeCfg<N>::THREADS, 1024 / PipeCfg<N>::THREADS) k_pipe(PipeArgs a) {
+  using P = PipeCfg<N>;
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int s_item, s_ready;
+  float2* tw = smem;
+  float2* bufs = smem + N;
+  for (int i = threadIdx.x; i < N; i += P::THREADS) tw[i] = a.tw[i];
+  const PipeSched<N, KIND> sc(a.S, a.D);
+  // second-phase items wait until every first-phase item of their slab is done
+  auto slab_of = [&](int item) {
+    int ph, s, j;
+    sc.decode(item, &ph, &s, &j);
+    return ph == 1 ? s : -1;
+  };
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = (int)atomicAdd(a.ctr, 1u);
+    s_item = it;
+    if (it < sc.total && slab_of(it) >= 0) wait_count(a.ctr + 1 + slab_of(it), sc.nA, a.wait_ns, a.err);
+  }
+  __syncthreads();
+  int cur = s_item;
+  if (cur < sc.total) pipe_issue<N, KIND>(a, sc, cur, bufs);
+  cp_async_commit();
+  for (int i = 0; cur < sc.total; ++i) {
+    float2* b = bufs + (i & 1) * P::BUF;
+    float2* bn = bufs + ((i + 1) & 1) * P::BUF;
+    __syncthreads();                       // bn (item i-1's buffer) and s_item are free
+    if (threadIdx.x == 0) {
+      const int it = (int)atomicAdd(a.ctr, 1u);
+      s_item = it;
+      const int sl = it < sc.total ? slab_of(it) : -1;
+      s_ready = sl < 0 || ld_acquire_u32(a.ctr + 1 + sl) >= (unsigned)sc.nA;
+    }
+    __syncthreads();
+    const int nxt = s_item;
+    const bool ready = s_ready != 0;
+    if (nxt < sc.total && ready) pipe_issue<N, KIND>(a, sc, nxt, bn);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    pipe_compute<N, KIND>(a, sc, cur, b, tw);
+    if (nxt < sc.total && !ready) {        // wait only while holding no unfinished item
+      if (threadIdx.x == 0) wait_count(a.ctr + 1 + slab_of(nxt), sc.nA, a.wait_ns, a.err);
+      __syncthreads();
+      pipe_issue<N, KIND>(a, sc, nxt, bn);
+      cp_async_commit();
+    }
+    cur = nxt;
+  }
+  cp_async_wait0();
 }
 
 // ---------------------------------------------------------------- host side
@@ -155,31 +253,40 @@ int fft_slab_planes(int n) {
 
 bool fft_has_potential(int n) { return is_pow2_size(n); }
 
-template <int N, bool INV>
-static int slab_launch(const FftTables& t, const float* rho, float2* spec, float* phi, unsigned* ctr, int* err,
-                       cudaStream_t s) {
-  using C = RegCfg<N>;
-  static int grid = 0;                      // per instantiation: device-independent here (one GPU type)
-  FPM_TRY(smem_attr(k_slab<N, INV>, C::SMEM));
+template <int N, int KIND>
+static int pipe_launch(const FftTables& t, const float* rho, float2* spec, float* phi, float coef, unsigned* ctr,
+                       int* err, cudaStream_t s) {
+  using P = PipeCfg<N>;
+  static int grid = 0;                      // blocks that fit the device at once (persistent)
+  FPM_TRY(smem_attr(k_pipe<N, KIND>, P::SMEM));
   if (grid == 0) {
     int dev = 0, nsm = 0, per = 0;
     FPM_CUDA_TRY(cudaGetDevice(&dev));
     FPM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slab<N, INV>, C::THREADS, C::SMEM));
+    FPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe<N, KIND>, P::THREADS, P::SMEM));
     if (per < 1) return FPM_ECUDA;
     grid = nsm * per;
   }
-  SlabArgs a;
+  PipeArgs a;
   a.rho = rho;
   a.spec = spec;
   a.phi = phi;
   a.tw = t.tw;
+  a.w2 = t.w2;
+  a.coef = coef;
   a.ctr = ctr;
   a.err = err;
-  a.S = fft_slab_planes(N);
-  a.spin_limit = 1ll << 20;
+  a.S = KIND == PK_X ? N : fft_slab_planes(N);
+  {
+    // lag: about three grids' worth of items between a slab's two phases
+    const int ns = N / a.S, ny = (a.S * P::NH + P::L - 1) / P::L, nz = a.S * P::ZI;
+    int D = 1;
+    while (D < ns && D * (ny + nz) < 3 * grid) ++D;
+    a.D = D;
+  }
+  a.wait_ns = 4000000000ll;
   FPM_CUDA_TRY(cudaMemsetAsync(ctr, 0, (size_t)(1 + N / a.S) * sizeof(unsigned), s));
-  k_slab<N, INV><<<grid, C::THREADS, C::SMEM, s>>>(a);
+  k_pipe<N, KIND><<<grid, P::THREADS, P::SMEM, s>>>(a);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
@@ -188,7 +295,7 @@ template <int N>
 static int pot_fwd_impl(const FftTables& t, const float* rho, float2* spec, unsigned* ctr, int* err,
                         cudaStream_t s) {
   if constexpr (is_pow2_size(N) && N >= 128) {
-    return slab_launch<N, false>(t, rho, spec, nullptr, ctr, err, s);
+    return pipe_launch<N, PK_FWD>(t, rho, spec, nullptr, 0.f, ctr, err, s);
   } else {
     FPM_TRY(fft_zfwd(t, rho, spec, 1, 0, 0, s));
     return fft_y(t, spec, 1, 0, false, s);
@@ -198,7 +305,7 @@ static int pot_fwd_impl(const FftTables& t, const float* rho, float2* spec, unsi
 template <int N>
 static int pot_inv_impl(const FftTables& t, float2* spec, float* phi, unsigned* ctr, int* err, cudaStream_t s) {
   if constexpr (is_pow2_size(N) && N >= 128) {
-    return slab_launch<N, true>(t, nullptr, spec, phi, ctr, err, s);
+    return pipe_launch<N, PK_INV>(t, nullptr, spec, phi, 0.f, ctr, err, s);
   } else {
     FPM_TRY(fft_y(t, spec, 1, 0, true, s));
     return fft_zinv(t, spec, phi, 1, 0, 0, s);
@@ -206,8 +313,10 @@ static int pot_inv_impl(const FftTables& t, float2* spec, float* phi, unsigned* 
 }
 
 template <int N>
-static int xgreen_impl(const FftTables& t, float2* spec, float coef, cudaStream_t s) {
-  if constexpr (is_pow2_size(N)) {
+static int xgreen_impl(const FftTables& t, float2* spec, float coef, unsigned* ctr, int* err, cudaStream_t s) {
+  if constexpr (is_pow2_size(N) && N >= 128) {
+    return pipe_launch<N, PK_X>(t, nullptr, spec, nullptr, coef, ctr, err, s);
+  } else if constexpr (is_pow2_size(N)) {
     using C = RegCfg<N>;
     FPM_TRY(smem_attr(k_xgreen_r<N>, C::SMEM));
     const int lines = (N / 2 + 1) * N;
@@ -246,8 +355,8 @@ int fft_pot_forward(const FftTables& t, const float* rho, float2* spec, unsigned
   FPM_DISPATCH_POW2(t.n, return pot_fwd_impl<N>(t, rho, spec, ctr, err, s));
 }
 
-int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, cudaStream_t s) {
-  FPM_DISPATCH_POW2(t.n, return xgreen_impl<N>(t, spec, coef, s));
+int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, unsigned* ctr, int* err, cudaStream_t s) {
+  FPM_DISPATCH_POW2(t.n, return xgreen_impl<N>(t, spec, coef, ctr, err, s));
 }
 
 int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr, int* err, cudaStream_t s) {

@@ -61,7 +61,7 @@ int fft_zinv3(const FftTables& t, const float2* spec, float4* out, size_t in_fs,
 bool fft_has_potential(int n);
 int fft_slab_planes(int n);
 int fft_pot_forward(const FftTables& t, const float* rho, float2* spec, unsigned* ctr, int* err, cudaStream_t s);
-int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, cudaStream_t s);
+int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, unsigned* ctr, int* err, cudaStream_t s);
 int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr, int* err, cudaStream_t s);
 // F: interleaved float4 per cell (f4) or [3][M].
 int fft_pot_gradient(const FftTables& t, const float* phi, float* F, bool f4, size_t M, cudaStream_t s);
