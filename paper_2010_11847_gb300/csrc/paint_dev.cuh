@@ -215,9 +215,11 @@ __device__ __forceinline__ void shell_decode(int s, int* l) {
 }
 
 // Deposit one warp's particles.  When the warp holds long runs of the same
-// local cell in adjacent lanes, each run is summed first (segmented
-// shuffle reduction; a run of <= 32 weights of <= 2^24 fits 32 bits) and
-// its head lane adds the 8 corner sums; otherwise every lane adds its own.
+// local cell in adjacent lanes (at most 8 distinct runs: dense clumps, where
+// same-address atomics would serialise), each run is summed first
+// (segmented shuffle reduction; a run of <= 32 weights of <= 2^24 fits 32
+// bits) and its head lane adds the 8 corner sums; otherwise every lane adds
+// its own.
 __device__ __forceinline__ void deposit_warp(uint32_t* lo, uint32_t* hi, bool active, const int* l,
                                              const float* t) {
   const unsigned full = 0xffffffffu;
@@ -234,7 +236,7 @@ __device__ __forceinline__ void deposit_warp(uint32_t* lo, uint32_t* hi, bool ac
   const bool head = (lane == 0) || (prev != key);
   const unsigned heads = __ballot_sync(full, head);
   const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
-  if (__popc(heads) > 24) {
+  if (__popc(heads) > 8) {
     if (active) {
 #pragma unroll
       for (int c = 0; c < 8; ++c)
@@ -269,22 +271,31 @@ __device__ __forceinline__ T ld_part(const T* p) {
   return __ldg(p);
 }
 
-// Local cell (relative to tile origin o) and fraction of particle i.
-template <bool COH>
-__device__ __forceinline__ bool particle_local(const float* __restrict__ dx, size_t N, uint32_t i,
-                                               const Geom& g, const int* o, int* l, float* t) {
+// Local cell (relative to tile origin o) and fraction of particle i at
+// displacement d.
+__device__ __forceinline__ bool local_cell(const float* d, uint32_t i, const Geom& g, const int* o, int* l,
+                                           float* t) {
   int q[3], c[3];
   lattice_node(i, g, q);
   bool ok = true;
-  for (int d = 0; d < 3; ++d) ok &= cic_cell(ld_part<COH>(dx + d * N + i), q[d], g.nc, &c[d], &t[d]);
-  for (int d = 0; d < 3; ++d) {
-    l[d] = c[d] - o[d];
-    if (l[d] < 0 || l[d] >= TILE) {   // cannot happen for a consistent key; guard anyway
+  for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], g.nc, &c[a], &t[a]);
+  for (int a = 0; a < 3; ++a) {
+    l[a] = c[a] - o[a];
+    if (l[a] < 0 || l[a] >= TILE) {   // cannot happen for a consistent key; guard anyway
       ok = false;
-      l[d] = 0;
+      l[a] = 0;
     }
   }
   return ok;
+}
+
+template <bool COH>
+__device__ __forceinline__ bool particle_local(const float* __restrict__ dx, size_t N, uint32_t i,
+                                               const Geom& g, const int* o, int* l, float* t) {
+  float d[3];   // the three gathers are issued back to back
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = ld_part<COH>(dx + a * N + i);
+  return local_cell(d, i, g, o, l, t);
 }
 
 // Write the tile's interior cells (final) and its 17^3 shell (partials).
@@ -407,7 +418,9 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
                                                  int iters, int bx) {
   // each CTA walks a contiguous chunk of iters*256 particles, so that the
   // force rows its neighbouring lattice rows share stay in its L1; the next
-  // chunk's dx and p are fetched while the current one gathers its forces
+  // chunk's dx and p are fetched while the current one gathers its forces.
+  // The particle arrays are streamed (evict-first) so that L2 keeps the
+  // force mesh.
   const int nc = g.nc;
   float K = 0.f, D = 0.f;
   if (KDK) {
@@ -421,8 +434,8 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
     if (i < N) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        dn[a] = dx[a * N + i];
-        if (KDK) pn[a] = p[a * N + i];
+        dn[a] = __ldcs(dx + a * N + i);
+        if (KDK) pn[a] = __ldcs(p + a * N + i);
       }
     }
   }
@@ -435,8 +448,8 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
     if (it + 1 < iters && inext < N) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        dn[a] = dx[a * N + inext];
-        if (KDK) pn[a] = p[a * N + inext];
+        dn[a] = __ldcs(dx + a * N + inext);
+        if (KDK) pn[a] = __ldcs(p + a * N + inext);
       }
     }
     int tile = 0;
@@ -466,9 +479,9 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const float pa = fmaf(K, f[a], pp[a]);
-          p[a * N + i] = pa;
+          __stcs(p + a * N + i, pa);
           d[a] = fmaf(D, pa, d[a]);
-          dx[a * N + i] = d[a];
+          __stcs(dx + a * N + i, d[a]);
         }
         if (keys) {
 #pragma unroll
