@@ -40,8 +40,8 @@ def _alg_bytes(cls, N, M, nc):
         "kdk_readout_kick_drift": 24 + 24 + 4 + 12 * M / N,   # dx,p r/w, key w, F read
         "cell_keys": 12 + 4,
         "tile_scan": 0.0,
-        "tile_scatter": 4 + 8,
-        "paint_tiles": 8 + 12 + 4 * M / N,
+        "tile_scatter": 4 + 4,                         # key read, item write
+        "paint_tiles": 4 + 12 + 4 * M / N,            # item, dx gather, rho write
         "paint_halo": 4 * M / N * 0.176,
         "fft_z_r2c": (4 + h) * M / N,
         "fft_y_fwd": 2 * h * M / N,
@@ -362,7 +362,8 @@ def run_fpm(args):
 
     for _ in range(max(args.warmup, 0)):
         one_sim(white)
-    assert plan.status() == 0, "device error flag set during warm-up"
+    st = plan.status()
+    assert st == 0, f"device error flag set during warm-up (status {st})"
 
     clocks = Clocks(local, enabled=not args.no_clocks and rank == 0)
     plan.profile(True)
@@ -386,7 +387,8 @@ def run_fpm(args):
     ms_step = float(t.item()) / args.steps
     pm_steps = wl.nsteps
     value = world * N * pm_steps / (ms_step / 1e3)
-    assert plan.status() == 0, "device error flag set during the timed run"
+    st = plan.status()
+    assert st == 0, f"device error flag set during the timed run (status {st})"
 
     # end to end: host white noise in, density and P(k) out, every step
     e2e = None
