@@ -333,9 +333,14 @@ int fpm_linear_field(fpm_plan* p, const float* white, void* lin_k, void* stream)
   const FftTables& t = p->tp;
   float2* out = reinterpret_cast<float2*>(lin_k);
   const double n3v = (double)p->N / (p->box * p->box * p->box);
-  return timed(p, FPM_K_IC, 3, s, [&] {
-    FPM_TRY(fft_zfwd(t, white, p->spec, 1, 0, 0, s));
-    FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+  const bool pot = fft_has_potential(p->np);
+  return timed(p, FPM_K_IC, pot && p->np >= 128 ? 2 : 3, s, [&] {
+    if (pot) {
+      FPM_TRY(fft_pot_forward(t, white, p->spec, p->slab_ctr, p->d_err, s));
+    } else {
+      FPM_TRY(fft_zfwd(t, white, p->spec, 1, 0, 0, s));
+      FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+    }
     return fft_xlinear(t, p->spec, out, p->eh, p->d_amp, (float)(6.283185307179586 / p->box), (float)n3v, s);
   });
 }
@@ -351,6 +356,30 @@ int fpm_lpt(fpm_plan* p, const void* lin_k, double a0, int order, float* dx, flo
   const float inv_n3 = (float)(1.0 / (double)p->N);
   const bool second = order == 2;
   const float r = (float)(p->nc / p->np);
+  if (ic_has_potential(p->np)) {
+    // psi = IFFT[lin / |w|^2] / N^3, S from its real-space second differences,
+    // then the displacement and momentum potentials and their Eq. 5 gradients
+    float* psi = p->real6;
+    float* phx = p->real6 + p->N;
+    float* php = p->real6 + 2 * p->N;
+    float2* s0 = p->spec;
+    float2* s1 = p->spec + p->specmax;
+    float2* s2 = p->spec + 2 * p->specmax;
+    const int fused = p->np >= 128 ? 1 : 2;
+    return timed(p, FPM_K_IC, second ? 5 + 4 * fused : 3 + 2 * fused, s, [&] {
+      if (second) {
+        FPM_TRY(fft_xpot(t, lk, s0, inv_n3, s));
+        FPM_TRY(fft_pot_inverse(t, s0, psi, p->slab_ctr, p->d_err, s));
+        FPM_TRY(launch_lpt_source_fd(p->np, psi, p->rho, s));
+        FPM_TRY(fft_pot_forward(t, p->rho, s0, p->slab_ctr, p->d_err, s));
+      }
+      FPM_TRY(fft_xdisp2(t, s0, lk, s1, s2, p->d_gr, (float)a0, inv_n3 * r, second, s));
+      FPM_TRY(fft_pot_inverse(t, s1, phx, p->slab_ctr, p->d_err, s));
+      FPM_TRY(fft_pot_inverse(t, s2, php, p->slab_ctr, p->d_err, s));
+      FPM_TRY(fft_pot_gradient(t, phx, dx, false, p->N, s));
+      return fft_pot_gradient(t, php, mom, false, p->N, s);
+    });
+  }
   return timed(p, FPM_K_IC, second ? 11 : 4, s, [&] {
     if (second) {
       FPM_TRY(fft_xlpt_hessian(t, lk, p->spec, p->specmax, inv_n3, s));
@@ -424,12 +453,19 @@ int fpm_power(fpm_plan* p, const float* a, const float* b, double* pk, double* k
   const int nb = p->nc / 2;
   FPM_CUDA_TRY(cudaMemsetAsync(p->d_bins, 0, 3 * nb * sizeof(double), s));
   float2* sb = b ? p->spec + p->specmax : nullptr;
-  FPM_TRY(timed(p, FPM_K_POWER, b ? 5 : 3, s, [&] {
-    FPM_TRY(fft_zfwd(t, a, p->spec, 1, 0, 0, s));
-    FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
-    if (b) {
-      FPM_TRY(fft_zfwd(t, b, sb, 1, 0, 0, s));
-      FPM_TRY(fft_y(t, sb, 1, 0, false, s));
+  const bool pot = fft_has_potential(p->nc);
+  const int zy = pot && p->nc >= 128 ? 1 : 2;
+  FPM_TRY(timed(p, FPM_K_POWER, b ? 1 + 2 * zy : 1 + zy, s, [&] {
+    if (pot) {
+      FPM_TRY(fft_pot_forward(t, a, p->spec, p->slab_ctr, p->d_err, s));
+      if (b) FPM_TRY(fft_pot_forward(t, b, sb, p->slab_ctr, p->d_err, s));
+    } else {
+      FPM_TRY(fft_zfwd(t, a, p->spec, 1, 0, 0, s));
+      FPM_TRY(fft_y(t, p->spec, 1, 0, false, s));
+      if (b) {
+        FPM_TRY(fft_zfwd(t, b, sb, 1, 0, 0, s));
+        FPM_TRY(fft_y(t, sb, 1, 0, false, s));
+      }
     }
     return fft_xpower(t, p->spec, sb, p->d_bins, s);
   }));
@@ -631,9 +667,16 @@ int fpm_lpt_adj(fpm_plan* p, const void* lin_k, double a0, int order, const floa
     int ns = 0;
     if (order == 2) {
       // phi_ij of the forward model, then g_S = sum_d B_d g_Psi2_d
-      FPM_TRY(fft_xlpt_hessian(t, lk, p->spec, p->specmax, inv_n3, s));
-      FPM_TRY(fft_y(t, p->spec, 6, p->specmax, true, s));
-      FPM_TRY(fft_zinv(t, p->spec, p->real6, 6, p->specmax, N, s));
+      if (ic_has_potential(p->np)) {
+        // psi = IFFT[lin / |w|^2] / N^3 in the gS slot, phi_ij from its second differences
+        FPM_TRY(fft_xpot(t, lk, p->spec, inv_n3, s));
+        FPM_TRY(fft_pot_inverse(t, p->spec, p->gS, p->slab_ctr, p->d_err, s));
+        FPM_TRY(launch_lpt_hessian_fd(p->np, p->gS, p->real6, s));
+      } else {
+        FPM_TRY(fft_xlpt_hessian(t, lk, p->spec, p->specmax, inv_n3, s));
+        FPM_TRY(fft_y(t, p->spec, 6, p->specmax, true, s));
+        FPM_TRY(fft_zinv(t, p->spec, p->real6, 6, p->specmax, N, s));
+      }
       FPM_TRY(fft_zfwd(t, p->adj6 + 3 * N, p->aspec, 3, N, sp, s));
       FPM_TRY(fft_y(t, p->aspec, 3, sp, false, s));
       for (int d = 0; d < 3; ++d) src[d] = XSource{p->aspec + d * sp, SK_B, d, 0, 0};

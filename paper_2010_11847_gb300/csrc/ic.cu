@@ -1,23 +1,14 @@
 // ic.cu -- linear field (Algorithm 4 steps 1-2), 2LPT displacements and
 // momenta (Algorithm 4 steps 3-6, second order per the LPT scaling test),
 // and the binned power spectrum used by Eqs. 10-11.  All of them are x-axis
-// passes of the 3D FFT with a spectral operator in the middle.
+// passes of the 3D FFT with a spectral operator in the middle.  Power-of-two
+// lattices use the register FFT and build 2LPT through potentials
+// (ic_reg.cuh); the shared-memory kernels below serve 48/96/192/384.
 #include "internal.h"
 #include "fft_passes.cuh"
+#include "ic_reg.cuh"
 
 namespace fpm {
-
-// Eisenstein & Hu (1998) no-wiggle transfer function in FP32 (their eqs.
-// 26, 28-31), k in h/Mpc.
-__device__ __forceinline__ float eh_nowiggle_T32(float k_h, const EhParams& e) {
-  const float ks = 0.43f * k_h * e.h * e.s;
-  const float ks2 = ks * ks;
-  const float gamma = e.omh * (e.alpha + (1.f - e.alpha) / (1.f + ks2 * ks2));
-  const float q = k_h * e.theta2 / gamma;
-  const float L0 = logf(5.43656365691809f + 1.8f * q);   // 2e + 1.8 q
-  const float C0 = 14.2f + 731.f / (1.f + 62.5f * q);
-  return L0 / (L0 + C0 * q * q);
-}
 
 // ------------------------------------------------------------ linear field
 // Forward x transform of DFT_zy(white), then scale each mode by
@@ -240,46 +231,77 @@ static int set_smem(K kernel, size_t bytes) {
 template <int N>
 static int xlinear_impl(const FftTables& t, const float2* in, float2* out, const EhParams& e,
                         const double* d_amp, float kf, float n3v, cudaStream_t s) {
-  const size_t sm = xpass_smem<N>(2);
-  FPM_TRY(set_smem(k_xlinear<N>, sm));
-  k_xlinear<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(in, out, e, d_amp, kf, n3v, t.tw);
-  FPM_CUDA_TRY(cudaGetLastError());
-  return FPM_OK;
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_xlin_r<N>, C::SMEM));
+    k_xlin_r<N><<<((N / 2 + 1) * N + C::L - 1) / C::L, C::THREADS, C::SMEM, s>>>(in, out, e, d_amp, kf, n3v, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  } else {
+    const size_t sm = xpass_smem<N>(2);
+    FPM_TRY(set_smem(k_xlinear<N>, sm));
+    k_xlinear<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(in, out, e, d_amp, kf, n3v, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
 }
 
 template <int N>
 static int xhess_impl(const FftTables& t, const float2* lin_k, float2* out, size_t out_fs, float coef,
                       cudaStream_t s) {
-  const size_t sm = xpass_smem<N>(3);
-  FPM_TRY(set_smem(k_xlpt_hessian<N>, sm));
-  k_xlpt_hessian<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(lin_k, out, out_fs, coef, t.tw, t.g, t.w2);
-  FPM_CUDA_TRY(cudaGetLastError());
-  return FPM_OK;
+  if constexpr (is_pow2_size(N)) {
+    return FPM_ENOTIMPL;                 // power-of-two lattices take the potential path
+  } else {
+    const size_t sm = xpass_smem<N>(3);
+    FPM_TRY(set_smem(k_xlpt_hessian<N>, sm));
+    k_xlpt_hessian<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(lin_k, out, out_fs, coef, t.tw, t.g, t.w2);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
 }
 
 template <int N>
 static int xdisp_impl(const FftTables& t, const float2* specS, const float2* lin_k, float2* out, size_t out_fs,
                       const double* gr, float a0, float coef, bool second, cudaStream_t s) {
-  const size_t sm = xpass_smem<N>(4);
-  const int grid = (N / 2 + 1) * (N / XB);
-  if (second) {
-    FPM_TRY(set_smem(k_xlpt_disp<N, true>, sm));
-    k_xlpt_disp<N, true><<<grid, FFT_THREADS, sm, s>>>(specS, lin_k, out, out_fs, gr, a0, coef, t.tw, t.g, t.w2);
+  if constexpr (is_pow2_size(N)) {
+    return FPM_ENOTIMPL;                 // power-of-two lattices take the potential path
   } else {
-    FPM_TRY(set_smem(k_xlpt_disp<N, false>, sm));
-    k_xlpt_disp<N, false><<<grid, FFT_THREADS, sm, s>>>(specS, lin_k, out, out_fs, gr, a0, coef, t.tw, t.g, t.w2);
+    const size_t sm = xpass_smem<N>(4);
+    const int grid = (N / 2 + 1) * (N / XB);
+    if (second) {
+      FPM_TRY(set_smem(k_xlpt_disp<N, true>, sm));
+      k_xlpt_disp<N, true><<<grid, FFT_THREADS, sm, s>>>(specS, lin_k, out, out_fs, gr, a0, coef, t.tw, t.g, t.w2);
+    } else {
+      FPM_TRY(set_smem(k_xlpt_disp<N, false>, sm));
+      k_xlpt_disp<N, false><<<grid, FFT_THREADS, sm, s>>>(specS, lin_k, out, out_fs, gr, a0, coef, t.tw, t.g, t.w2);
+    }
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
   }
-  FPM_CUDA_TRY(cudaGetLastError());
-  return FPM_OK;
 }
 
 template <int N>
 static int xpower_impl(const FftTables& t, const float2* sa, const float2* sb, double* bins, cudaStream_t s) {
-  const size_t sm = xpass_smem<N>(4) + 3 * (N / 2) * sizeof(double);
-  FPM_TRY(set_smem(k_xpower<N>, sm));
-  k_xpower<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(sa, sb, bins, t.tw);
-  FPM_CUDA_TRY(cudaGetLastError());
-  return FPM_OK;
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    const size_t sm = C::SMEM + 3 * (N / 2) * sizeof(double);
+    FPM_TRY(set_smem(k_xpow_r<N>, sm));
+    int dev = 0, nsm = 0, per = 0;
+    FPM_CUDA_TRY(cudaGetDevice(&dev));
+    FPM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_xpow_r<N>, C::THREADS, sm));
+    const int items = ((N / 2 + 1) * N + C::L - 1) / C::L;
+    const int grid = per > 0 && nsm * per < items ? nsm * per : items;
+    k_xpow_r<N><<<grid, C::THREADS, sm, s>>>(sa, sb, bins, t.tw, items);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  } else {
+    const size_t sm = xpass_smem<N>(4) + 3 * (N / 2) * sizeof(double);
+    FPM_TRY(set_smem(k_xpower<N>, sm));
+    k_xpower<N><<<(N / 2 + 1) * (N / XB), FFT_THREADS, sm, s>>>(sa, sb, bins, t.tw);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
 }
 
 int fft_xlinear(const FftTables& t, const float2* in, float2* out, const EhParams& e, const double* d_amp,
@@ -299,6 +321,71 @@ int fft_xlpt_disp(const FftTables& t, const float2* specS, const float2* lin_k, 
 
 int fft_xpower(const FftTables& t, const float2* sa, const float2* sb, double* bins, cudaStream_t s) {
   FPM_DISPATCH_N(t.n, return xpower_impl<N>(t, sa, sb, bins, s));
+}
+
+// ------------------------------------------------------------ 2LPT through potentials (power-of-two lattices)
+bool ic_has_potential(int n) { return is_pow2_size(n); }
+
+template <int N>
+static int xpot_impl(const FftTables& t, const float2* lin, float2* out, float coef, cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    FPM_TRY(set_smem(k_xpot_r<N>, C::SMEM));
+    k_xpot_r<N><<<((N / 2 + 1) * N + C::L - 1) / C::L, C::THREADS, C::SMEM, s>>>(lin, out, coef, t.tw, t.w2);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  return FPM_ENOTIMPL;
+}
+
+template <int N>
+static int xdisp2_impl(const FftTables& t, const float2* specS, const float2* lin, float2* out0, float2* out1,
+                       const double* gr, float a0, float coef, bool second, cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using C = RegCfg<N>;
+    const size_t sm = C::SMEM + (size_t)N * C::L * sizeof(float2);
+    const int grid = ((N / 2 + 1) * N + C::L - 1) / C::L;
+    if (second) {
+      FPM_TRY(set_smem(k_xdisp_r<N, true>, sm));
+      k_xdisp_r<N, true><<<grid, C::THREADS, sm, s>>>(specS, lin, out0, out1, gr, a0, coef, t.tw, t.w2);
+    } else {
+      FPM_TRY(set_smem(k_xdisp_r<N, false>, sm));
+      k_xdisp_r<N, false><<<grid, C::THREADS, sm, s>>>(specS, lin, out0, out1, gr, a0, coef, t.tw, t.w2);
+    }
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  return FPM_ENOTIMPL;
+}
+
+template <int N>
+static int source_fd_impl(const float* psi, float* S, bool hess, cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    using H = HsCfg<N>;
+    const dim3 grid(N / H::TZ, N / H::TY, N / H::XC);
+    if (hess) k_lpt_source_fd<N, true><<<grid, 256, 0, s>>>(psi, S);
+    else k_lpt_source_fd<N, false><<<grid, 256, 0, s>>>(psi, S);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  return FPM_ENOTIMPL;
+}
+
+int fft_xpot(const FftTables& t, const float2* lin, float2* out, float coef, cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return xpot_impl<N>(t, lin, out, coef, s));
+}
+
+int fft_xdisp2(const FftTables& t, const float2* specS, const float2* lin, float2* out0, float2* out1,
+               const double* gr, float a0, float coef, bool second, cudaStream_t s) {
+  FPM_DISPATCH_N(t.n, return xdisp2_impl<N>(t, specS, lin, out0, out1, gr, a0, coef, second, s));
+}
+
+int launch_lpt_source_fd(int n, const float* psi, float* S, cudaStream_t s) {
+  FPM_DISPATCH_N(n, return source_fd_impl<N>(psi, S, false, s));
+}
+
+int launch_lpt_hessian_fd(int n, const float* psi, float* phi6, cudaStream_t s) {
+  FPM_DISPATCH_N(n, return source_fd_impl<N>(psi, phi6, true, s));
 }
 
 int launch_lpt_source(const float* phi, size_t n, float* S, cudaStream_t s) {

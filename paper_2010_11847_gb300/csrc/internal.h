@@ -75,6 +75,16 @@ int fft_xlpt_disp(const FftTables& t, const float2* specS, const float2* lin_k, 
                   const double* gr, float a0, float coef, bool second, cudaStream_t s);
 int fft_xpower(const FftTables& t, const float2* sa, const float2* sb, double* bins, cudaStream_t s);
 int launch_lpt_source(const float* phi, size_t n, float* S, cudaStream_t s);
+// 2LPT through potentials (power-of-two lattices): psi = IFFT[coef lin/|w|^2]
+// (x pass), the real-space source S of psi, and the two potentials of the
+// displacement and the momentum (x pass with both outputs).
+bool ic_has_potential(int n);
+int fft_xpot(const FftTables& t, const float2* lin, float2* out, float coef, cudaStream_t s);
+int fft_xdisp2(const FftTables& t, const float2* specS, const float2* lin, float2* out0, float2* out1,
+               const double* gr, float a0, float coef, bool second, cudaStream_t s);
+int launch_lpt_source_fd(int n, const float* psi, float* S, cudaStream_t s);
+// the six phi_ij = IFFT[g_i g_j lin / |w|^2] / N^3 from psi, [6][n^3] (00, 11, 22, 01, 02, 12)
+int launch_lpt_hessian_fd(int n, const float* psi, float* phi6, cudaStream_t s);
 
 // paint.cu
 int paint_setup();
