@@ -347,6 +347,38 @@ def test_force_is_four_point_difference_of_potential():
         np.testing.assert_allclose(F[d], stencil, atol=1e-13)
 
 
+def test_lpt_fields_are_real_space_differences_of_one_potential():
+    """The 2LPT operators of the oracle (spectral g_i g_j / |w|^2 and
+    i g_d / |w|^2) equal real-space four-point differences of
+    psi = IFFT(delta_L / |w|^2): phi_ij = -D_i D_j psi, Psi1_d = D_d psi, and
+    Psi2_d = D_d phi2 with phi2 = -IFFT(S(k) / |w|^2) -- the form the CUDA path
+    evaluates for power-of-two lattices."""
+    n, box = 16, 100.0
+    lk = O.linear_field(inputs.white_noise(n, 29), box, COSMO)
+    psi1, psi2 = O.lpt_fields(lk)
+    k = 2 * math.pi * np.fft.fftfreq(n)
+    kz = 2 * math.pi * np.fft.rfftfreq(n)
+    KX, KY, KZ = np.meshgrid(k, k, kz, indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    k2[0, 0, 0] = 1.0
+    inv = 1.0 / k2
+    inv[0, 0, 0] = 0.0
+    psi = np.fft.irfftn(lk * inv, s=(n, n, n), axes=(0, 1, 2))
+
+    def D(f, ax):
+        r = lambda s: np.roll(f, -s, axis=ax)
+        return (8 * (r(1) - r(-1)) - (r(2) - r(-2))) / 12
+
+    ph = {(i, j): -D(D(psi, i), j) for i in range(3) for j in range(i, 3)}
+    S = (ph[0, 0] * ph[1, 1] + ph[0, 0] * ph[2, 2] + ph[1, 1] * ph[2, 2]
+         - ph[0, 1] ** 2 - ph[0, 2] ** 2 - ph[1, 2] ** 2)
+    phi2 = -np.fft.irfftn(np.fft.rfftn(S) * inv, s=(n, n, n), axes=(0, 1, 2))
+    scale = np.abs(psi1).max()
+    for d in range(3):
+        np.testing.assert_allclose(psi1[d], D(psi, d), atol=1e-12 * scale)
+        np.testing.assert_allclose(psi2[d], D(phi2, d), atol=1e-12 * max(np.abs(psi2).max(), 1e-30))
+
+
 def _ewald_force(r, L, m, om, alpha=None):
     """Periodic point-mass acceleration at displacement r from the source,
     for lap phi = 1.5 Om (rho - mean), by Ewald summation."""
