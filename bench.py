@@ -206,29 +206,28 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def kernel_source_hash():
+def kernel_source_hash(files):
+    """Hash of the CUDA sources a kernel class is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2010_11847_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(cls):
-    """DRAM bytes per launch of kernel class `cls` from the committed ncu
-    summary, when it was taken on the current kernel sources."""
+    """DRAM bytes per full-size launch of kernel class `cls` from the committed
+    ncu summary, when it was taken on the current sources of that kernel."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path))
+        e = json.load(open(path)).get("kernels", {}).get(cls)
     except ValueError:
         return None
-    if d.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(e.get("files", [])):
         return None
-    e = d.get("kernels", {}).get(cls)
-    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+    return e.get("dram_bytes_per_launch_full_size")
 
 
 def measure_batched(reps=3):

@@ -284,7 +284,7 @@ template <int N>
 static int xpower_impl(const FftTables& t, const float2* sa, const float2* sb, double* bins, cudaStream_t s) {
   if constexpr (is_pow2_size(N)) {
     using C = RegCfg<N>;
-    const size_t sm = C::SMEM + 3 * (N / 2) * sizeof(double);
+    const size_t sm = C::SMEM + 3 * (N / 2) * sizeof(float);
     FPM_TRY(set_smem(k_xpow_r<N>, sm));
     int dev = 0, nsm = 0, per = 0;
     FPM_CUDA_TRY(cudaGetDevice(&dev));

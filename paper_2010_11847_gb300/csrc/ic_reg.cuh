@@ -158,10 +158,12 @@ __device__ __forceinline__ void body_xdisp_r(const float2* specS, const float2* 
 // Binned power: forward x transform of DFT_zy(a) (and b); every mode adds
 // w Re(A B*), w and w |n| to bin j (j - 1/2 <= |n| < j + 1/2, 1 <= j <= N/2),
 // w = 2 for 0 < kz < N/2 (the conjugate partner), else 1.  acc: 3 N/2
-// doubles of shared memory, flushed by the caller.
+// floats of shared memory (native shared atomics; a block's partial sums of
+// at most a few thousand positive terms per bin), flushed in FP64 by the
+// caller.
 template <int N>
 __device__ __forceinline__ void body_xpow_r(const float2* __restrict__ sa, const float2* __restrict__ sb,
-                                            double* acc, const float2* __restrict__ g_tw, float2* smem, int bx) {
+                                            float* acc, const float2* __restrict__ g_tw, float2* smem, int bx) {
   using X = XLine<N>;
   constexpr int NBIN = N / 2;
   float2* tw = smem;
@@ -180,7 +182,7 @@ __device__ __forceinline__ void body_xpow_r(const float2* __restrict__ sa, const
 #pragma unroll
     for (int s = 0; s < 8; ++s) B[s] = A[s];
   }
-  const double w = (x.kz > 0 && x.kz < N / 2) ? 2.0 : 1.0;
+  const float w = (x.kz > 0 && x.kz < N / 2) ? 2.f : 1.f;
   const int fy = freq_of(x.ky, N);
   const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -191,9 +193,9 @@ __device__ __forceinline__ void body_xpow_r(const float2* __restrict__ sa, const
     if ((2 * b - 1) * (2 * b - 1) > 4 * n2) --b;
     if ((2 * b + 1) * (2 * b + 1) <= 4 * n2) ++b;
     const bool in = x.valid && b >= 1 && b <= NBIN;
-    double v0 = in ? w * ((double)A[s].x * B[s].x + (double)A[s].y * B[s].y) : 0.0;
-    double v1 = in ? w : 0.0;
-    double v2 = in ? w * sqrt((double)n2) : 0.0;
+    float v0 = in ? w * (A[s].x * B[s].x + A[s].y * B[s].y) : 0.f;
+    float v1 = in ? w : 0.f;
+    float v2 = in ? w * sqrtf((float)n2) : 0.f;
     // neighbouring lanes usually share the bin: then one atomic per warp
     const int b0 = __shfl_sync(full, b, 0);
     if (__all_sync(full, in && b == b0)) {
@@ -351,17 +353,17 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
              const float2* __restrict__ g_tw, int items) {
   extern __shared__ float2 smem[];
   constexpr int NBIN = N / 2;
-  double* acc = reinterpret_cast<double*>(smem + N + RegCfg<N>::L * rline<N>());
+  float* acc = reinterpret_cast<float*>(smem + N + RegCfg<N>::L * rline<N>());
   float2* tw = smem;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
-  for (int k = threadIdx.x; k < 3 * NBIN; k += blockDim.x) acc[k] = 0.0;
+  for (int k = threadIdx.x; k < 3 * NBIN; k += blockDim.x) acc[k] = 0.f;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     __syncthreads();
     body_xpow_r<N>(sa, sb, acc, g_tw, smem, it);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < 3 * NBIN; k += blockDim.x)
-    if (acc[k] != 0.0) atomicAdd(bins + k, acc[k]);
+    if (acc[k] != 0.f) atomicAdd(bins + k, (double)acc[k]);
 }
 
 }  // namespace fpm
