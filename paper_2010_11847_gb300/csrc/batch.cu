@@ -211,7 +211,7 @@ static void items_for(SimDesc& d, int ro_iters) {
   d.items_of[PH_KDK] = (int)((d.N + pchunk - 1) / pchunk);
   d.items_of[PH_KDK_LAST] = d.items_of[PH_KDK];
   d.items_of[PH_SCAN] = 1;
-  d.items_of[PH_SCATTER] = (int)((d.N + (size_t)BT * 4 - 1) / ((size_t)BT * 4));
+  d.items_of[PH_SCATTER] = (int)((d.N + (size_t)BT * SCAT_E - 1) / ((size_t)BT * SCAT_E));
   d.items_of[PH_PAINT] = d.ntiles;
   d.items_of[PH_HALO] = d.ntiles;
   int L = 0;

@@ -27,9 +27,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int N>
+// Lines per block: the x pass keeps RegCfg's (64-byte rows at N = 512); the
+// z and y passes at N = 512 take 4 lines (256 threads), so that a block
+// barrier waits on fewer warps and more blocks interleave (measured faster).
+template <int N, bool XP = false>
 struct PipeCfg {
-  static constexpr int T = RegCfg<N>::T, L = RegCfg<N>::L, THREADS = RegCfg<N>::THREADS;
+  static constexpr int T = RegCfg<N>::T;
+  static constexpr int L = (!XP && N == 512) ? 4 : RegCfg<N>::L;
+  static constexpr int THREADS = T * L;
   static constexpr int NH = N / 2 + 1;
   static constexpr int RL = N + 2;                  // line-major exchange (swizzled), 16-byte aligned
   static constexpr int RLX = N + N / 8 + (N == 128 ? 1 : 2);   // x pass exchange (padded)
@@ -74,7 +79,7 @@ __device__ __forceinline__ void issue_zi(const float2* spec, size_t r0, float2* 
 
 template <int N>
 __device__ __forceinline__ void issue_x(const float2* spec, int gl0, float2* buf) {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, true>;
   constexpr int L = P::L, CPK = L / 2;
   constexpr size_t S = (size_t)P::NH * N;
   for (int c = threadIdx.x; c < N * CPK; c += P::THREADS) {
@@ -180,7 +185,7 @@ __device__ __forceinline__ void comp_zi(float* phi, size_t r0, float2* buf, cons
 template <int N>
 __device__ __forceinline__ void comp_x(float2* spec, int gl0, float coef, float2* buf, const float2* tw,
                                        const float* __restrict__ g_w2) {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, true>;
   constexpr int T = P::T, L = P::L;
   constexpr size_t S = (size_t)P::NH * N;
   const int line = threadIdx.x % L, t = threadIdx.x / L;

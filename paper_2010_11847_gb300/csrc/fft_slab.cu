@@ -101,7 +101,7 @@ template <int N>
 __device__ __forceinline__ void discard_z_item(const float2* spec, int bx) {
   using P = PipeCfg<N>;
   constexpr int NH = P::NH, LPR = (2 * P::L * 8) / 128;
-  static_assert((2 * P::L * 8) % 128 == 0, "z item rows must cover whole lines");
+  if ((2 * P::L * 8) % 128 != 0) return;   // a line is shared with the next item: keep it
   const size_t r0 = (size_t)bx * 2 * P::L;
   const size_t x = r0 / N, y0 = r0 - x * N;
   for (int e = threadIdx.x; e < NH * LPR; e += blockDim.x) {
@@ -117,7 +117,7 @@ enum PipeKind : int { PK_FWD = 0, PK_INV = 1, PK_X = 2 };
 // c2r to phi (ZI); PK_X: x items only, no dependencies.
 template <int N, int KIND>
 struct PipeSched {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, KIND == PK_X>;
   int S, ns, D, nA, nB, total;
   __device__ PipeSched(int S_, int D_) : S(S_), ns(N / S_), D(D_) {
     const int ny = (S * P::NH + P::L - 1) / P::L, nz = S * P::ZI;
@@ -143,7 +143,7 @@ struct PipeSched {
 
 template <int N, int KIND>
 __device__ __forceinline__ void pipe_issue(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item, float2* buf) {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, KIND == PK_X>;
   int ph, s, j;
   sc.decode(item, &ph, &s, &j);
   float2* slab = a.spec + (size_t)s * sc.S * P::NH * N;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void pipe_issue(const PipeArgs& a, const PipeSched<N,
 template <int N, int KIND>
 __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item,
                                              float2* buf, const float2* tw) {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, KIND == PK_X>;
   int ph, s, j;
   sc.decode(item, &ph, &s, &j);
   float2* slab = a.spec + (size_t)s * sc.S * P::NH * N;
@@ -182,8 +182,9 @@ __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<
 }
 
 template <int N, int KIND>
-__global__ void __launch_bounds__(PipeCfg<N>::THREADS, 1024 / PipeCfg<N>::THREADS) k_pipe(PipeArgs a) {
-  using P = PipeCfg<N>;
+__global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS, 1024 / PipeCfg<N, KIND == PK_X>::THREADS)
+    k_pipe(PipeArgs a) {
+  using P = PipeCfg<N, KIND == PK_X>;
   extern __shared__ __align__(16) float2 smem[];
   __shared__ int s_item, s_ready;
   float2* tw = smem;
@@ -256,7 +257,7 @@ bool fft_has_potential(int n) { return is_pow2_size(n); }
 template <int N, int KIND>
 static int pipe_launch(const FftTables& t, const float* rho, float2* spec, float* phi, float coef, unsigned* ctr,
                        int* err, cudaStream_t s) {
-  using P = PipeCfg<N>;
+  using P = PipeCfg<N, KIND == PK_X>;
   static int grid = 0;                      // blocks that fit the device at once (persistent)
   FPM_TRY(smem_attr(k_pipe<N, KIND>, P::SMEM));
   if (grid == 0) {
