@@ -102,6 +102,7 @@ void free_plan(fpm_plan* p) {
   cudaFree(p->pc.tile_count);
   cudaFree(p->pc.tile_start);
   cudaFree(p->pc.tile_cursor);
+  cudaFree(p->pc.tile_done);
   cudaFree(p->pc.halo);
   cudaFree(p->pc.big_flag);
   cudaFree(p->d_amp);
@@ -203,7 +204,7 @@ int sort_paint_impl(fpm_plan* p, const PaintCtx& c, const float* dx, float* rho,
   FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
   FPM_TRY(timed(p, FPM_K_PAINT, 1, s, [&] { return launch_paint_tiles(c, dx, rho, perm, s); }));
   if (perm) FPM_TRY(timed(p, FPM_K_PAINT, 1, s, [&] { return launch_perm_big(c, perm, s); }));
-  FPM_TRY(timed(p, FPM_K_HALO, 1, s, [&] { return launch_halo(c, rho, s); }));
+  if (perm || !c.tile_done) FPM_TRY(timed(p, FPM_K_HALO, 1, s, [&] { return launch_halo(c, rho, s); }));
   return FPM_OK;
 }
 
@@ -286,6 +287,8 @@ int fpm_plan_create(fpm_plan** out, int np, int nc, double box, const fpm_cosmo*
   TRY(dalloc(p, &c.tile_start, (size_t)c.ntiles + 1));
   TRY(dalloc(p, &c.tile_cursor, (size_t)c.ntiles));
   TRY(dalloc(p, &c.halo, paint_halo_elems(c.ntiles)));
+  TRY(dalloc(p, &c.tile_done, (size_t)c.ntiles));
+  if (cudaMemsetAsync(c.tile_done, 0, sizeof(uint32_t) * c.ntiles, s) != cudaSuccess) TRY(FPM_ECUDA);
   TRY(dalloc(p, &c.big_flag, 1));
   TRY(dalloc(p, &p->d_amp, 1));
   TRY(dalloc(p, &p->d_pts, 2 * MAX_STEPS + 2));

@@ -33,6 +33,8 @@ struct PaintCtx {
   uint32_t* tile_start = nullptr;  // [ntiles + 1]
   uint32_t* tile_cursor = nullptr; // [ntiles]
   unsigned long long* halo = nullptr;  // [ntiles * SHELL] fixed-point shell partials
+  uint32_t* tile_done = nullptr;   // [ntiles] shells counted toward each tile's faces (zero between paints);
+                                   // null: the faces are summed by a separate halo launch
   int* err = nullptr;
   int* big_flag = nullptr;
 };

@@ -55,6 +55,19 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __rest
   body_paint_bucket(dx, N, items, tile_start, g, rho, halo, err, lo, hi, blockIdx.x);
 }
 
+// Paint with the face sums done by the last contributing block.
+__global__ void __launch_bounds__(PB_THREADS) k_paint_bucket_faces(const float* __restrict__ dx, size_t N,
+                                                                   const uint32_t* __restrict__ items,
+                                                                   const uint32_t* __restrict__ tile_start, Geom g,
+                                                                   float* __restrict__ rho,
+                                                                   unsigned long long* __restrict__ halo,
+                                                                   uint32_t* __restrict__ done, int* __restrict__ err) {
+  __shared__ uint32_t lo[ACC], hi[ACC];
+  __shared__ uint32_t sm[24];
+  body_paint_bucket(dx, N, items, tile_start, g, rho, halo, err, lo, hi, blockIdx.x);
+  paint_faces_last(done, halo, g, rho, blockIdx.x, sm);
+}
+
 __global__ void __launch_bounds__(768) k_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
                                                     float* __restrict__ rho) {
   __shared__ uint32_t nb[8];
@@ -258,6 +271,9 @@ int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t*
   if (perm) {
     k_paint_sorted<<<c.ntiles, PS_THREADS, SORTED_SMEM, s>>>(dx, c.N, c.items, c.keys, c.tile_start, c.g, rho,
                                                               c.halo, perm, c.err);
+  } else if (c.tile_done) {
+    k_paint_bucket_faces<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo,
+                                                          c.tile_done, c.err);
   } else {
     k_paint_bucket<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo, c.err);
   }

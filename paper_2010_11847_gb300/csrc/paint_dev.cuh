@@ -384,10 +384,47 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
     for (int b = 0; b < 8; ++b) {
       const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
       if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
-      sum += halo[(size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz)];
+      sum += __ldcg(halo + (size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz));
     }
     rho[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
         from_fix(sum, g.mass);
+  }
+}
+
+// Faces summed by the last contributor.  A tile's lower-face cells receive
+// the shells of the tile and of its 7 lower neighbours; after a block has
+// written its shell it counts it toward the 8 tiles T + {0,1}^3 its 17^3
+// block overlaps, and the block whose count completes a tile (the 8th)
+// sums that tile's faces at once, while the partials are still in L2 --
+// no separate launch and no waiting.  Release: every thread's stores, block
+// barrier, fence, count; acquire: count seen at 7, fence, block barrier.
+// The finisher resets the count for the next paint.  sm: 24 words of
+// shared memory.
+__device__ __forceinline__ void paint_faces_last(uint32_t* __restrict__ done, const unsigned long long* halo,
+                                                 const Geom& g, float* __restrict__ rho, int tile, uint32_t* sm) {
+  const int nt = g.nt;
+  uint32_t* nb = sm;                 // 8 words: neighbour tiles of the face sum
+  uint32_t* list = sm + 8;           // up to 8 completed tiles
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
+    uint32_t nl = 0;
+    __threadfence();
+    for (int b = 0; b < 8; ++b) {
+      const int x = tc[0] + (b >> 2), y = tc[1] + ((b >> 1) & 1), z = tc[2] + (b & 1);
+      const int u = ((x == nt ? 0 : x) * nt + (y == nt ? 0 : y)) * nt + (z == nt ? 0 : z);
+      if (atomicAdd(done + u, 1u) == 7u) list[nl++] = (uint32_t)u;
+    }
+    __threadfence();
+    sm[16] = nl;
+  }
+  __syncthreads();
+  const uint32_t nl = sm[16];
+  for (uint32_t k = 0; k < nl; ++k) {
+    const int u = (int)list[k];
+    body_paint_halo(halo, g, rho, nb, u);
+    __syncthreads();
+    if (threadIdx.x == 0) done[u] = 0u;
   }
 }
 
