@@ -108,31 +108,50 @@ __device__ __forceinline__ void body_keys(const float* __restrict__ dx, Geom g, 
 }
 
 // ---------------------------------------------------------------- scan of tile counts
-// part: blockDim.x words of shared memory.  With zero_counts the consumed
-// counts are cleared for the next histogram.
+// Each warp scans a contiguous segment of the counts in coalesced rounds of
+// 32 (shuffle scan with a running carry), the warp totals are scanned in
+// shared memory, and a second pass adds each warp's offset.  part: blockDim/32
+// + 1 words of shared memory.  With zero_counts the consumed counts are
+// cleared for the next histogram.
 __device__ __forceinline__ void body_scan_tiles(uint32_t* __restrict__ count, int ntiles, uint32_t* __restrict__ start,
                                                 uint32_t* __restrict__ cursor, uint32_t* part, int zero_counts) {
-  const int nth = blockDim.x;
-  const int per = (ntiles + nth - 1) / nth;
-  const int b = threadIdx.x * per;
-  uint32_t s = 0;
-  for (int k = 0; k < per && b + k < ntiles; ++k) s += count[b + k];
-  part[threadIdx.x] = s;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = ((ntiles + nw - 1) / nw + 31) & ~31;
+  const int b0 = warp * seg, b1 = min(b0 + seg, ntiles);
+  uint32_t carry = 0;
+  for (int b = b0; b < b1; b += 32) {
+    const int i = b + lane;
+    const uint32_t v = i < b1 ? __ldcg(count + i) : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(full, x, off);
+      if (lane >= off) x += y;
+    }
+    if (i < b1) start[i] = carry + x - v;
+    carry += __shfl_sync(full, x, 31);
+  }
+  if (lane == 0) part[warp] = carry;
   __syncthreads();
-  for (int off = 1; off < nth; off <<= 1) {      // Hillis-Steele inclusive scan
-    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < nw; ++w) {
+      const uint32_t t = part[w];
+      part[w] = run;
+      run += t;
+    }
+    part[nw] = run;
   }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (int k = 0; k < per && b + k < ntiles; ++k) {
-    start[b + k] = run;
-    cursor[b + k] = run;
-    run += count[b + k];
-    if (zero_counts) count[b + k] = 0;
+  __syncthreads();
+  const uint32_t off = part[warp];
+  for (int i = b0 + lane; i < b1; i += 32) {
+    const uint32_t v = start[i] + off;
+    start[i] = v;
+    cursor[i] = v;
+    if (zero_counts) count[i] = 0u;
   }
-  if (threadIdx.x == nth - 1) start[ntiles] = part[nth - 1];
+  if (threadIdx.x == 0) start[ntiles] = part[nw];
 }
 
 // ---------------------------------------------------------------- bucket by tile
