@@ -91,6 +91,35 @@ def dist():
     return rank, world, local
 
 
+# ---------------------------------------------------------------- replicas (N > 1)
+# Every rank runs its own simulation (its own seed): no data-path collective;
+# the only exchange is the max of the per-rank times.
+def rank_seed(seed, rank):
+    return seed + rank
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """Largest value of x over all ranks (x itself when world == 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, particles, pm_steps, seconds):
+    """Whole-job particle-steps/s: every rank advanced `particles` for
+    `pm_steps` steps; the job took the slowest rank's time."""
+    return world * particles * pm_steps / seconds
+
+
+def shard(items, rank, world):
+    """Items (e.g. the simulations of a batch) assigned to one rank."""
+    return items[rank::world]
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -340,7 +369,7 @@ def run_fpm(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     plan = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
-    white_h = torch.from_numpy(inputs.white_noise(wl.np_, wl.seed + rank)).pin_memory()
+    white_h = torch.from_numpy(inputs.white_noise(wl.np_, rank_seed(wl.seed, rank))).pin_memory()
     white = white_h.to(dev)
     lin_k = torch.empty(plan.spectrum_shape(), dtype=torch.complex64, device=dev)
     dx = torch.empty(3, N, device=dev)
@@ -379,13 +408,10 @@ def run_fpm(args):
     launches = launch_count() - launches0
     prof = plan.profile_read()
     plan.profile(False)
-    ms_total = e0.elapsed_time(e1)
-    t = torch.tensor([ms_total], device=dev)
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    ms_step = ms_total / args.steps
     pm_steps = wl.nsteps
-    value = world * N * pm_steps / (ms_step / 1e3)
+    value = job_value(world, N, pm_steps, ms_step / 1e3)
     st = plan.status()
     assert st == 0, f"device error flag set during the timed run (status {st})"
 
@@ -434,12 +460,8 @@ def run_fpm(args):
                 down[j].record(copy)
         copy.synchronize()
         barrier()
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device=dev)
-        if world > 1:
-            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": world * N * pm_steps * args.steps / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_value(world, N, pm_steps * args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(white_h.numel() * 4),
                "d2h_bytes_per_step": int(rho_h[0].numel() * 4 + 3 * 8 * (wl.nc // 2))}
 
