@@ -542,6 +542,17 @@ static int ensure_adjoint(fpm_plan* p) {
 // g_rho = -sum_d A_d g_F_d (A_d^T = -A_d for the real odd force kernels).
 static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream_t s) {
   const FftTables& t = p->tc;
+  if (fft_has_potential(t.n)) {
+    // F_d = D_d G rho with G symmetric and D^T = -D: g_rho = G (-sum_d D_d g_F_d)
+    const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
+    const int fused = t.n >= 128 ? 1 : 2;
+    FPM_TRY(timed(p, FPM_K_POT_GRAD, 1, s, [&] { return fft_pot_divergence_neg(t, gF, g_rho, s); }));
+    FPM_TRY(timed(p, FPM_K_POT_FWD, fused, s,
+                  [&] { return fft_pot_forward(t, g_rho, p->spec, p->slab_ctr, p->d_err, s); }));
+    FPM_TRY(timed(p, FPM_K_POT_X, 1, s, [&] { return fft_pot_xgreen(t, p->spec, coef, p->slab_ctr, p->d_err, s); }));
+    return timed(p, FPM_K_POT_INV, fused, s,
+                 [&] { return fft_pot_inverse(t, p->spec, g_rho, p->slab_ctr, p->d_err, s); });
+  }
   FPM_TRY(timed(p, FPM_K_FFT_ZF, 1, s, [&] { return fft_zfwd(t, gF, p->spec, 3, p->M, p->specmax, s); }));
   FPM_TRY(timed(p, FPM_K_FFT_YF, 1, s, [&] { return fft_y(t, p->spec, 3, p->specmax, false, s); }));
   XSource src[3];

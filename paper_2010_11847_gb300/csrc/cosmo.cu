@@ -36,14 +36,52 @@ __device__ __forceinline__ void growth_rhs(const GrowthCoef& c, const double* y,
 
 // One CTA per scale factor a_in[0..n]; a_in[n] must be 1 (the
 // normalisation point).  raw[4*i..]: D1, dD1/dlna, D2, dD2/dlna unnormalised.
-// The ODE coefficients at all 2*RK4_CHAIN+1 half-step points are computed
-// by the whole CTA first (they do not depend on the solution); one thread
-// then runs the dependent RK4 chain with multiply-adds only.
+// Each target integrates from A_INIT with RK4_CHAIN RK4 steps of size h in
+// ln a.  The ODE coefficients at the 2*RK4_CHAIN+1 half-step points do not
+// depend on the solution and are computed by the whole CTA first.  The
+// chain is then evaluated in parallel, with the same discretisation: the
+// D1 system is linear, so each RK4 step is a 2x2 matrix A_s (the same
+// matrix acts on the homogeneous part of D2); an exclusive prefix scan of
+// the A_s gives D1 at every step start, from which each step's D2 source
+// increment b_s follows; the D2 steps are affine maps y -> A_s y + b_s,
+// composed by an ordered reduction.  Only the association of the FP64
+// products differs from the serial chain.
 constexpr int RK4_CHAIN = 1024;
 constexpr int GROWTH_THREADS = 256;
+constexpr int STEPS_PER_THREAD = RK4_CHAIN / GROWTH_THREADS;
+
+struct M2 {
+  double a, b, c, d;   // [[a b] [c d]]
+};
+__device__ __forceinline__ M2 mmul(const M2& x, const M2& y) {   // x * y
+  return M2{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+__device__ __forceinline__ void mvec(const M2& m, double u, double v, double* ou, double* ov) {
+  *ou = m.a * u + m.b * v;
+  *ov = m.c * u + m.d * v;
+}
+
+// One RK4 step of the 4-state system from y (D1, D1', D2, D2'); the D2
+// source uses the D1 stage values, as the serial chain does.
+__device__ __forceinline__ void rk4_step(const GrowthCoef& cs, const GrowthCoef& cm, const GrowthCoef& ce, double h,
+                                         double* y) {
+  double k1[4], k2[4], k3[4], k4[4], t[4];
+  growth_rhs(cs, y, k1);
+  for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+  growth_rhs(cm, t, k2);
+  for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+  growth_rhs(cm, t, k3);
+  for (int i = 0; i < 4; ++i) t[i] = y[i] + h * k3[i];
+  growth_rhs(ce, t, k4);
+  for (int i = 0; i < 4; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
 __global__ void __launch_bounds__(GROWTH_THREADS) k_growth_raw(const double* __restrict__ a_in, double om,
                                                                double* __restrict__ raw) {
   __shared__ double c1[2 * RK4_CHAIN + 1], c2[2 * RK4_CHAIN + 1];
+  __shared__ double scratch[GROWTH_THREADS * 6];
+  M2* pre = reinterpret_cast<M2*>(scratch);                         // D1 scan: products of each thread's steps
+  double(*aff)[6] = reinterpret_cast<double(*)[6]>(scratch);      // then the D2 reduction: affine maps (M2, b)
   const double lna0 = log(A_INIT);
   const double h = (log(a_in[blockIdx.x]) - lna0) / RK4_CHAIN;
   for (int j = threadIdx.x; j <= 2 * RK4_CHAIN; j += blockDim.x) {
@@ -52,22 +90,84 @@ __global__ void __launch_bounds__(GROWTH_THREADS) k_growth_raw(const double* __r
     c2[j] = c.c2;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double a = A_INIT;
-  double y[4] = {a, a, -3.0 / 7.0 * a * a, -6.0 / 7.0 * a * a};
-  for (int s = 0; s < RK4_CHAIN; ++s) {
-    const GrowthCoef cs{c1[2 * s], c2[2 * s]}, cm{c1[2 * s + 1], c2[2 * s + 1]}, ce{c1[2 * s + 2], c2[2 * s + 2]};
-    double k1[4], k2[4], k3[4], k4[4], t[4];
-    growth_rhs(cs, y, k1);
-    for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k1[i];
-    growth_rhs(cm, t, k2);
-    for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * h * k2[i];
-    growth_rhs(cm, t, k3);
-    for (int i = 0; i < 4; ++i) t[i] = y[i] + h * k3[i];
-    growth_rhs(ce, t, k4);
-    for (int i = 0; i < 4; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  const int tid = threadIdx.x, s0 = tid * STEPS_PER_THREAD;
+  auto coefs = [&](int s, GrowthCoef* cs, GrowthCoef* cm, GrowthCoef* ce) {
+    *cs = GrowthCoef{c1[2 * s], c2[2 * s]};
+    *cm = GrowthCoef{c1[2 * s + 1], c2[2 * s + 1]};
+    *ce = GrowthCoef{c1[2 * s + 2], c2[2 * s + 2]};
+  };
+  // step matrices of the linear part: the RK4 step applied to the unit vectors
+  M2 A[STEPS_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < STEPS_PER_THREAD; ++q) {
+    GrowthCoef cs, cm, ce;
+    coefs(s0 + q, &cs, &cm, &ce);
+    double e1[4] = {1.0, 0.0, 0.0, 0.0}, e2[4] = {0.0, 1.0, 0.0, 0.0};
+    rk4_step(cs, cm, ce, h, e1);
+    rk4_step(cs, cm, ce, h, e2);
+    A[q] = M2{e1[0], e2[0], e1[1], e2[1]};
   }
-  for (int k = 0; k < 4; ++k) raw[4 * blockIdx.x + k] = y[k];
+  // exclusive scan of the products (later steps multiply from the left)
+  M2 local = A[0];
+#pragma unroll
+  for (int q = 1; q < STEPS_PER_THREAD; ++q) local = mmul(A[q], local);
+  pre[tid] = local;
+  __syncthreads();
+  for (int off = 1; off < GROWTH_THREADS; off <<= 1) {   // inclusive Hillis-Steele: pre[t] = P(t) ... P(0)
+    const M2 other = tid >= off ? pre[tid - off] : M2{1.0, 0.0, 0.0, 1.0};
+    __syncthreads();
+    pre[tid] = mmul(pre[tid], other);
+    __syncthreads();
+  }
+  const M2 before = tid ? pre[tid - 1] : M2{1.0, 0.0, 0.0, 1.0};
+  __syncthreads();                              // pre is reused as aff below
+  // D1 state at each of this thread's step starts; D2 source increments
+  const double a0 = A_INIT;
+  double u, v;
+  mvec(before, a0, a0, &u, &v);                 // y1 = (D1, D1') at step s0
+  M2 Q{1.0, 0.0, 0.0, 1.0};
+  double bu = 0.0, bv = 0.0;                    // this thread's composed D2 affine map: y2 -> Q y2 + (bu, bv)
+#pragma unroll
+  for (int q = 0; q < STEPS_PER_THREAD; ++q) {
+    GrowthCoef cs, cm, ce;
+    coefs(s0 + q, &cs, &cm, &ce);
+    double y[4] = {u, v, 0.0, 0.0};
+    rk4_step(cs, cm, ce, h, y);                 // D2 part: the source increment b_s (zero D2 start)
+    double nu, nv;
+    mvec(A[q], bu, bv, &nu, &nv);
+    bu = nu + y[2];
+    bv = nv + y[3];
+    Q = mmul(A[q], Q);
+    u = y[0];
+    v = y[1];
+  }
+  aff[tid][0] = Q.a; aff[tid][1] = Q.b; aff[tid][2] = Q.c; aff[tid][3] = Q.d;
+  aff[tid][4] = bu; aff[tid][5] = bv;
+  __syncthreads();
+  // ordered reduction: (Q2, b2) after (Q1, b1) = (Q2 Q1, Q2 b1 + b2)
+  for (int w = 1; w < GROWTH_THREADS; w <<= 1) {
+    if ((tid & (2 * w - 1)) == 0) {
+      const double* L = aff[tid];
+      const double* R = aff[tid + w];
+      const M2 q1{L[0], L[1], L[2], L[3]}, q2{R[0], R[1], R[2], R[3]};
+      const M2 q = mmul(q2, q1);
+      double nu, nv;
+      mvec(q2, L[4], L[5], &nu, &nv);
+      aff[tid][0] = q.a; aff[tid][1] = q.b; aff[tid][2] = q.c; aff[tid][3] = q.d;
+      aff[tid][4] = nu + R[4];
+      aff[tid][5] = nv + R[5];
+    }
+    __syncthreads();
+  }
+  if (tid == GROWTH_THREADS - 1) {              // the last thread holds D1 at the end of the chain
+    const M2 q{aff[0][0], aff[0][1], aff[0][2], aff[0][3]};
+    double d2u, d2v;
+    mvec(q, -3.0 / 7.0 * a0 * a0, -6.0 / 7.0 * a0 * a0, &d2u, &d2v);
+    raw[4 * blockIdx.x + 0] = u;
+    raw[4 * blockIdx.x + 1] = v;
+    raw[4 * blockIdx.x + 2] = d2u + aff[0][4];
+    raw[4 * blockIdx.x + 3] = d2v + aff[0][5];
+  }
 }
 
 // out[6*i..]: D1, D2, f1, f2, E, dD1/da, normalised by row n (a = 1).

@@ -472,6 +472,30 @@ __device__ __forceinline__ void body_stencil(const float* __restrict__ phi, floa
   }
 }
 
+// Transpose of the gradient: out = -sum_d D_d g_d for g = [3][N^3] (D is
+// antisymmetric: D^T = -D).  One cell per thread; the neighbour loads of a
+// warp are coalesced along z and shared through L1.
+template <int N>
+__global__ void __launch_bounds__(256) k_div_neg(const float* __restrict__ g, float* __restrict__ out) {
+  constexpr size_t M = (size_t)N * N * N;
+  const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= M) return;
+  const int z = (int)(i % N), y = (int)((i / N) % N), x = (int)(i / ((size_t)N * N));
+  auto at = [](int xx, int yy, int zz) {
+    return ((size_t)(xx & (N - 1)) * N + (yy & (N - 1))) * N + (zz & (N - 1));
+  };
+  const float* gx = g;
+  const float* gy = g + M;
+  const float* gz = g + 2 * M;
+  const float dx_ = fd4(__ldg(gx + at(x - 2, y, z)), __ldg(gx + at(x - 1, y, z)), __ldg(gx + at(x + 1, y, z)),
+                        __ldg(gx + at(x + 2, y, z)));
+  const float dy_ = fd4(__ldg(gy + at(x, y - 2, z)), __ldg(gy + at(x, y - 1, z)), __ldg(gy + at(x, y + 1, z)),
+                        __ldg(gy + at(x, y + 2, z)));
+  const float dz_ = fd4(__ldg(gz + at(x, y, z - 2)), __ldg(gz + at(x, y, z - 1)), __ldg(gz + at(x, y, z + 1)),
+                        __ldg(gz + at(x, y, z + 2)));
+  out[i] = -(dx_ + dy_ + dz_);
+}
+
 template <int N, bool F4>
 __global__ void __launch_bounds__(256) k_stencil(const float* __restrict__ phi, float* __restrict__ F, size_t M) {
   __shared__ float ring[5 * StCfg<N>::PLANE];

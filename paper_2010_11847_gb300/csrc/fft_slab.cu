@@ -364,6 +364,21 @@ int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr,
   FPM_DISPATCH_POW2(t.n, return pot_inv_impl<N>(t, spec, phi, ctr, err, s));
 }
 
+template <int N>
+static int div_impl(const float* g, float* out, cudaStream_t s) {
+  if constexpr (is_pow2_size(N)) {
+    const size_t M = (size_t)N * N * N;
+    k_div_neg<N><<<(unsigned)((M + 255) / 256), 256, 0, s>>>(g, out);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
+  return FPM_ENOTIMPL;
+}
+
+int fft_pot_divergence_neg(const FftTables& t, const float* g, float* out, cudaStream_t s) {
+  FPM_DISPATCH_POW2(t.n, return div_impl<N>(g, out, s));
+}
+
 int fft_pot_gradient(const FftTables& t, const float* phi, float* F, bool f4, size_t M, cudaStream_t s) {
   FPM_DISPATCH_POW2(t.n, return stencil_impl<N>(phi, F, f4, M, s));
 }

@@ -67,6 +67,8 @@ int fft_pot_xgreen(const FftTables& t, float2* spec, float coef, unsigned* ctr, 
 int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr, int* err, cudaStream_t s);
 // F: interleaved float4 per cell (f4) or [3][M].
 int fft_pot_gradient(const FftTables& t, const float* phi, float* F, bool f4, size_t M, cudaStream_t s);
+// out = -sum_d D_d g_d, g = [3][n^3]: the transpose of the gradient
+int fft_pot_divergence_neg(const FftTables& t, const float* g, float* out, cudaStream_t s);
 
 // ic.cu
 int fft_xlinear(const FftTables& t, const float2* in, float2* out, const EhParams& e, const double* d_amp,
