@@ -351,6 +351,38 @@ def measure_fwd_adjoint(wl, reps=1):
             "particle_steps_per_s_fwd_adj": wl.np_ ** 3 * wl.nsteps / (out["fwd_adj"] / 1e3)}
 
 
+def measure_reconstruction(iters=10, warmup=2):
+    """Adam iterations of the Sec. 7.1 reconstruction (forward with checkpoints,
+    adjoint, fused Adam + prior) at 128^3 particles on 128^3 cells, 400 Mpc/h,
+    5 KDK steps, against a target density from another seed."""
+    import torch
+    from paper_2010_11847_gb300 import inputs
+    from paper_2010_11847_gb300.binding import Plan
+    from paper_2010_11847_gb300.reconstruct import Reconstruction
+    wl = inputs.DIFFERENTIABLE
+    stages = wl.stages()
+    pl = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    wt = torch.from_numpy(inputs.white_noise(wl.np_, wl.seed + 1)).cuda()
+    lk = pl.linear_field(wt)
+    dx, p = pl.lpt(lk, float(stages[0]), 2)
+    pl.kdk(dx, p, stages)
+    target = pl.paint(dx) - 1.0
+    rec = Reconstruction(pl, target, stages, torch.zeros_like(wt), lr=0.01)
+    first = rec.step()
+    for _ in range(warmup - 1):
+        rec.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        last = rec.step()
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / iters
+    pl.close()
+    return {"workload": wl.name, "ms_per_iteration": ms, "iterations": iters,
+            "neg_log_posterior_first": first, "neg_log_posterior_last": last,
+            "paper_context": "about 1.1 s per iteration on one V100 (another machine; context only)"}
+
+
 def run_fpm(args):
     import numpy as np
     import torch
@@ -497,6 +529,7 @@ def run_fpm(args):
         torch.cuda.empty_cache()
         from paper_2010_11847_gb300 import inputs as _in
         extra["fwd_adjoint"] = measure_fwd_adjoint(wl)
+        extra["reconstruction"] = measure_reconstruction()
         # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
         # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
         extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)

@@ -150,6 +150,20 @@ int fpm_power(fpm_plan* plan, const float* a, const float* b, double* pk,
  * capture).  All return-by-argument buffers are overwritten unless stated.
  * ------------------------------------------------------------------- */
 
+/* One Adam update (Kingma & Ba 2015, Algorithm 1; the optimiser of the
+ * paper's reconstruction, Sec. 7.1, learning rate 0.01 there) on the
+ * negative log-posterior of Eq. 12, with the prior of the white noise fused:
+ * the gradient used is gscale * g + pscale * x (g: DEVICE float[n], e.g.
+ * d chi^2 / d x; gscale = 1/2, pscale = 1 give chi^2/2 + x^T x/2).  x, m, v
+ * (DEVICE float[n]) are updated in place; t >= 1 is the step count (bias
+ * corrections 1/(1 - beta^t)).  prior (nullable, HOST double) receives the
+ * FP64 sum of x^2 / 2 before the update; when given, `stream` is
+ * synchronised.  FPM_EINVAL for n <= 0, t < 1, lr <= 0, beta outside [0, 1)
+ * or eps < 0.  Asynchronous otherwise. */
+int fpm_adam_step(fpm_plan* plan, float* x, const float* g, float* m, float* v, int64_t n, double gscale,
+                  double pscale, double lr, double beta1, double beta2, double eps, int t, double* prior,
+                  void* stream);
+
 /* chi^2 of Eq. 12's likelihood term: loss = sum_c (rho_c - 1 - t_c)^2 /
  * sigma^2 with t = target_delta (float[nc^3]), accumulated in FP64 in a
  * fixed order; g_rho (nullable, float[nc^3]) = 2 (rho - 1 - t) / sigma^2.

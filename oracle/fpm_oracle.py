@@ -735,3 +735,30 @@ def chi2_and_grad(white, delta_target, nc, box, cosmo, stages, sigma=1.0, order=
     g_dx0, g_p0 = kdk_adj(xs, stages, g_dx, np.zeros_like(g_dx), np_, nc, cosmo["omega_m"])
     G = lpt_adj(lin_k, nc, stages[0], cosmo, g_dx0, g_p0, order=order)
     return loss, linear_field_adj(G, box, cosmo)
+
+
+# ---------------------------------------------------------------------------
+# Reconstruction (Sec. 7.1, Eq. 12): negative log-posterior and Adam
+# ---------------------------------------------------------------------------
+def posterior_and_grad(white, delta_target, nc, box, cosmo, stages, sigma=1.0, order=2):
+    """Eq. 12's negative log-posterior of the initial conditions and its
+    gradient with respect to the white noise w:
+
+      -log p = chi^2 / 2 + s^dagger S^-1 s / 2,   chi^2 = sum (delta - delta_t)^2 / sigma^2.
+
+    The initial field is s = L w with L diagonal in Fourier space and S = L L^dagger
+    the fiducial covariance, so s^dagger S^-1 s = w^T w (the prior of the white noise)."""
+    loss, g = chi2_and_grad(white, delta_target, nc, box, cosmo, stages, sigma=sigma, order=order)
+    w = np.asarray(white, dtype=np.float64)
+    return 0.5 * loss + 0.5 * float((w * w).sum()), 0.5 * g + w
+
+
+def adam_step(x, g, m, v, t, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1; the
+    paper's optimiser with learning rate 0.01 (Sec. 7.1).  Returns (x, m, v)."""
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return np.asarray(x, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -26,7 +26,7 @@ EXPORTS = [
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
     "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
     "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
-    "fpm_batch_status", "fpm_batch_info",
+    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step",
 ]
 FPM_K_COUNT = 19
 
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_launch_count.restype = i64
     L.fpm_paint_noalloc.argtypes = [i, i, vp, vp, vp]
     L.fpm_chi2.argtypes = [vp, vp, vp, d, vp, vp, vp]
+    L.fpm_adam_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64, d, d, d, d, d, d, ctypes.c_int, vp, vp]
     L.fpm_paint_adj.argtypes = [vp, vp, vp, vp, vp]
     L.fpm_readout_adj.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_force_adj.argtypes = [vp, vp, vp, vp]
@@ -239,6 +240,17 @@ class Plan:
         _check("fpm_chi2", lib().fpm_chi2(self._h, _ptr(rho), _ptr(target_delta), float(sigma),
                                           _ptr(g_rho) if want_grad else None, ctypes.byref(loss), _stream(stream)))
         return loss.value, g_rho
+
+    def adam_step(self, x, g, m, v, t, lr=0.01, betas=(0.9, 0.999), eps=1e-8, gscale=1.0, pscale=0.0,
+                  want_prior=True, stream=None):
+        """One Adam update of x in place with the gradient gscale g + pscale x
+        (Eq. 12's prior on the white noise); returns sum(x^2)/2 before it."""
+        prior = ctypes.c_double()
+        _check("fpm_adam_step", lib().fpm_adam_step(self._h, _ptr(x), _ptr(g), _ptr(m), _ptr(v), int(x.numel()),
+                                                    float(gscale), float(pscale), float(lr), float(betas[0]),
+                                                    float(betas[1]), float(eps), int(t),
+                                                    ctypes.byref(prior) if want_prior else None, _stream(stream)))
+        return prior.value if want_prior else None
 
     def paint_adj(self, dx, g_rho, g_dx=None, stream=None):
         g_dx = g_dx if g_dx is not None else self._empty(3, self.N)

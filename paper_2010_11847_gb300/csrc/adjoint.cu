@@ -169,6 +169,48 @@ int launch_chi2(const float* rho, const float* target, size_t M, float sigma, fl
   return FPM_OK;
 }
 
+// ------------------------------------------------------------ Adam on the posterior (Sec. 7.1, Eq. 12)
+// g' = gscale g + pscale x (the prior term of the white noise), then one Adam
+// update (Kingma & Ba 2015, Algorithm 1) of x, m, v in place; c1, c2 are the
+// bias corrections 1/(1 - beta^t) and o1, o2 = 1 - beta, all formed in FP64
+// on the host (1 - 0.999f in float32 would be off by 1e-5).  The FP64 sum of x^2 / 2 before the update
+// (the prior's value) goes to per-block partials in a fixed order.
+__global__ void __launch_bounds__(CHI_THREADS) k_adam(float* __restrict__ x, const float* __restrict__ g,
+                                                      float* __restrict__ m, float* __restrict__ v, size_t n,
+                                                      float gscale, float pscale, float lr, float b1, float b2,
+                                                      float o1, float o2, float eps, float c1, float c2,
+                                                      double* __restrict__ partial) {
+  __shared__ double sm[CHI_THREADS];
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float xi = x[i];
+    acc += 0.5 * (double)xi * (double)xi;
+    const float gi = fmaf(gscale, g[i], pscale * xi);
+    const float mi = fmaf(b1, m[i], o1 * gi);
+    const float vi = fmaf(b2, v[i], o2 * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    x[i] = xi - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = CHI_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+int launch_adam(float* x, const float* g, float* m, float* v, size_t n, float gscale, float pscale, float lr,
+                float b1, float b2, float o1, float o2, float eps, float c1, float c2, double* partial, int npartial,
+                double* prior, cudaStream_t s) {
+  k_adam<<<npartial, CHI_THREADS, 0, s>>>(x, g, m, v, n, gscale, pscale, lr, b1, b2, o1, o2, eps, c1, c2, partial);
+  FPM_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<1, CHI_THREADS, 0, s>>>(partial, npartial, prior);
+  FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
 // ------------------------------------------------------------ reverse kick / drift
 // gp += D gx (drift transpose), then v = K gp with K = fac[ik1] (+ fac[ik2]).
 __global__ void k_adj_drift_kick(float* __restrict__ gx, float* __restrict__ gp, float* __restrict__ v, size_t n,

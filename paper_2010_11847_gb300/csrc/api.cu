@@ -591,6 +591,26 @@ int fpm_chi2(fpm_plan* p, const float* rho, const float* target, double sigma, f
   return FPM_OK;
 }
 
+int fpm_adam_step(fpm_plan* p, float* x, const float* g, float* m, float* v, int64_t n, double gscale,
+                  double pscale, double lr, double beta1, double beta2, double eps, int t, double* prior,
+                  void* stream) {
+  if (!p || !x || !g || !m || !v || n <= 0 || t < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) ||
+      !(beta2 >= 0 && beta2 < 1) || !(eps >= 0))
+    return FPM_EINVAL;
+  FPM_TRY(ensure_adjoint(p));
+  cudaStream_t s = S(stream);
+  const double c1 = 1.0 / (1.0 - pow(beta1, t)), c2 = 1.0 / (1.0 - pow(beta2, t));
+  FPM_TRY(launch_adam(x, g, m, v, (size_t)n, (float)gscale, (float)pscale, (float)lr, (float)beta1, (float)beta2,
+                      (float)(1.0 - beta1), (float)(1.0 - beta2), (float)eps, (float)c1, (float)c2, p->partial,
+                      CHI_PARTIALS, p->d_loss, s));
+  g_launches += 2;
+  if (prior) {
+    FPM_CUDA_TRY(cudaMemcpyAsync(prior, p->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return FPM_OK;
+}
+
 int fpm_paint_adj(fpm_plan* p, const float* dx, const float* g_rho, float* g_dx, void* stream) {
   if (!p || !dx || !g_rho || !g_dx) return FPM_EINVAL;
   cudaStream_t s = S(stream);

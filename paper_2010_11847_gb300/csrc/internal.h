@@ -129,6 +129,9 @@ constexpr int XCOMBINE_MAX = 9;
 // inverse != 0 (out stays in k space otherwise).  out may alias a source.
 int fft_xcombine(const FftTables& t, const XSource* src, int nsrc, float coef, double omega_m, const EhParams* eh,
                  const double* d_amp, float kf, float n3v, float2* out, int inverse, cudaStream_t s);
+int launch_adam(float* x, const float* g, float* m, float* v, size_t n, float gscale, float pscale, float lr,
+                float b1, float b2, float o1, float o2, float eps, float c1, float c2, double* partial, int npartial,
+                double* prior, cudaStream_t s);
 int launch_chi2(const float* rho, const float* target, size_t M, float sigma, float* g_rho, double* partial,
                 int npartial, double* loss, cudaStream_t s);
 int launch_adj_drift_kick(float* gx, float* gp, float* v, size_t n, const double* fac, int idr, int ik1, int ik2,
