@@ -251,9 +251,36 @@ def fd_gradient_kernel_half(n):
     return g
 
 
-def _gradient_kernels(n):
-    g = fd_gradient_kernel(n)
-    gz = fd_gradient_kernel_half(n)
+def exact_gradient_kernel(n):
+    """The exact derivative of the band-limited interpolant, i w with
+    w = 2 pi n_d / N in cell units.  At the Nyquist frequency a real field's
+    derivative has no real representative, so the value there is set to 0
+    (the force variant of Sec. 2 with the continuous i k)."""
+    f = _freq_int(n)
+    w = 2.0 * math.pi * f / n
+    w[f == -n // 2] = 0.0
+    return w
+
+
+def exact_gradient_kernel_half(n):
+    """``exact_gradient_kernel`` on the last (half) axis, frequencies 0..n/2."""
+    fz = np.arange(n // 2 + 1)
+    w = 2.0 * math.pi * fz / n
+    w[fz == n // 2] = 0.0
+    return w
+
+
+GRADIENTS = ("fd4", "exact")     # Eq. 5's four-point difference; the exact i k
+GREENS = ("naive", "discrete")   # -1/k^2; Eq. 4's discrete Laplacian
+
+
+def _gradient_kernels(n, gradient="fd4"):
+    if gradient == "fd4":
+        g, gz = fd_gradient_kernel(n), fd_gradient_kernel_half(n)
+    elif gradient == "exact":
+        g, gz = exact_gradient_kernel(n), exact_gradient_kernel_half(n)
+    else:
+        raise ValueError(gradient)
     return g[:, None, None], g[None, :, None], gz[None, None, :]
 
 
@@ -263,6 +290,23 @@ def _laplacian_naive(n):
     nx, ny, nz = half_spectrum_wavenumbers(n)
     c = 2.0 * math.pi / n
     return (c * nx) ** 2 + (c * ny) ** 2 + (c * nz) ** 2
+
+
+def _laplacian_discrete(n):
+    """Eq. 4's denominator: sum_d (w_d sinc(w_d / 2))^2 = sum_d (2 sin(w_d / 2))^2
+    (sinc x = sin x / x), the symbol of the seven-point discrete Laplacian in
+    cell units (x0 = 1)."""
+    nx, ny, nz = half_spectrum_wavenumbers(n)
+    c = math.pi / n
+    return sum((2.0 * np.sin(c * v)) ** 2 for v in (nx, ny, nz))
+
+
+def _laplacian(n, green="naive"):
+    if green == "naive":
+        return _laplacian_naive(n)
+    if green == "discrete":
+        return _laplacian_discrete(n)
+    raise ValueError(green)
 
 
 # ---------------------------------------------------------------------------
@@ -438,43 +482,46 @@ def readout(F, dx, np_, nc):
 # ---------------------------------------------------------------------------
 # Force (Eqs. 3-5 with the naive Green's function)
 # ---------------------------------------------------------------------------
-def force_from_delta(delta, omega_m):
+def force_from_delta(delta, omega_m, green="naive", gradient="fd4"):
     """F_d = IFFT( i g_d(w) * 1.5 Om * FFT(delta) / |w|^2 ),  F(k=0) = 0.
 
     Eq. 3 (f = grad grad^-2 delta) with the Poisson factor and sign of
-    F = -grad phi, lap phi = 1.5 Om delta; grad^-2 is the naive -1/k^2 and
-    grad the FD kernel of Eq. 5.  Cell units, H0 = 1.
+    F = -grad phi, lap phi = 1.5 Om delta.  Default: grad^-2 is the naive
+    -1/k^2 and grad the FD kernel of Eq. 5.  Variants: green="discrete" puts
+    Eq. 4's discrete Laplacian in the denominator; gradient="exact" uses
+    g_d = w_d (Nyquist 0).  Cell units, H0 = 1.
     """
     n = delta.shape[0]
     dk = _rfftn(delta)
-    g = _gradient_kernels(n)
-    k2 = _laplacian_naive(n)
+    g = _gradient_kernels(n, gradient)
+    k2 = _laplacian(n, green)
     k2[0, 0, 0] = 1.0
     pot = 1.5 * omega_m * dk / k2
     pot[0, 0, 0] = 0.0
     return np.stack([_irfftn(1j * g[d] * pot, n) for d in range(3)])
 
 
-def force(rho, omega_m):
+def force(rho, omega_m, green="naive", gradient="fd4"):
     """Force meshes from a density mesh (delta = rho - 1)."""
-    return force_from_delta(np.asarray(rho, dtype=np.float64) - 1.0, omega_m)
+    return force_from_delta(np.asarray(rho, dtype=np.float64) - 1.0, omega_m, green, gradient)
 
 
-def particle_force(dx, np_, nc, omega_m):
+def particle_force(dx, np_, nc, omega_m, green="naive", gradient="fd4"):
     """paint -> force -> readout for particles at displacements dx."""
-    return readout(force(paint(dx, np_, nc), omega_m), dx, np_, nc)
+    return readout(force(paint(dx, np_, nc), omega_m, green, gradient), dx, np_, nc)
 
 
 # ---------------------------------------------------------------------------
 # Time integration: KDK leapfrog (Eqs. 1-2)
 # ---------------------------------------------------------------------------
-def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None):
+def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None, green="naive", gradient="fd4"):
     """Run len(stages)-1 KDK steps from (dx, p) at stages[0].
 
     The oracle performs the two half kicks of every step separately.  The
     particle-to-cell assignment uses the float32 value of dx (as the GPU
     stores it) when ``round_to_float32``; all arithmetic is FP64.
     ``record``, if a list, receives (dx, p) at the start of every step.
+    ``green`` and ``gradient`` select the force variant (``force_from_delta``).
     """
     kick1, drift, kick2 = fastpm_factors(stages, omega_m)
     dx = np.array(dx, dtype=np.float64)
@@ -482,7 +529,7 @@ def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None):
 
     def frc(x):
         xx = x.astype(np.float32) if round_to_float32 else x
-        return particle_force(xx, np_, nc, omega_m)
+        return particle_force(xx, np_, nc, omega_m, green, gradient)
 
     f = frc(dx)
     for k in range(len(stages) - 1):
@@ -619,13 +666,14 @@ def readout_adj(F, dx, g_f, np_, nc):
     return g_F, g_dx
 
 
-def force_adj(g_F, omega_m):
+def force_adj(g_F, omega_m, green="naive", gradient="fd4"):
     """Transpose of delta -> F (Eqs. 3-5): each F_d is a convolution with a
     real odd kernel, so its transpose is its negative:
-    g_delta = -sum_d IFFT(i g_d 1.5 Om FFT(g_F_d) / |w|^2)."""
+    g_delta = -sum_d IFFT(i g_d 1.5 Om FFT(g_F_d) / |w|^2).  Both variants
+    keep the kernel real and odd (g_d odd in w_d, the Laplacian even)."""
     n = g_F.shape[-1]
-    g = _gradient_kernels(n)
-    k2 = _laplacian_naive(n)
+    g = _gradient_kernels(n, gradient)
+    k2 = _laplacian(n, green)
     k2[0, 0, 0] = 1.0
     acc = 0.0
     for d in range(3):
@@ -635,15 +683,15 @@ def force_adj(g_F, omega_m):
     return -_irfftn(acc, n)
 
 
-def particle_force_adj(dx, g_f, np_, nc, omega_m):
+def particle_force_adj(dx, g_f, np_, nc, omega_m, green="naive", gradient="fd4"):
     """Transposed Jacobian of dx -> particle_force(dx) applied to g_f."""
-    F = force(paint(dx, np_, nc), omega_m)
+    F = force(paint(dx, np_, nc), omega_m, green, gradient)
     g_F, g_dx = readout_adj(F, dx, g_f, np_, nc)
-    g_rho = force_adj(g_F, omega_m)
+    g_rho = force_adj(g_F, omega_m, green, gradient)
     return g_dx + paint_adj(g_rho, dx, np_, nc)
 
 
-def kdk_adj(xs, stages, g_dx, g_p, np_, nc, omega_m):
+def kdk_adj(xs, stages, g_dx, g_p, np_, nc, omega_m, green="naive", gradient="fd4"):
     """Reverse of ``kdk`` given the positions x_k at every stage (xs[k],
     float32-rounded as the forward used them) and the cotangents of the final
     (dx, p).  Undoes, for k = n-1..0: the closing kick at x_{k+1}, the drift,
@@ -653,9 +701,9 @@ def kdk_adj(xs, stages, g_dx, g_p, np_, nc, omega_m):
     gp = np.array(g_p, dtype=np.float64)
     n = len(stages) - 1
     for k in range(n - 1, -1, -1):
-        gx = gx + particle_force_adj(xs[k + 1], kick2[k] * gp, np_, nc, omega_m)
+        gx = gx + particle_force_adj(xs[k + 1], kick2[k] * gp, np_, nc, omega_m, green, gradient)
         gp = gp + drift[k] * gx
-        gx = gx + particle_force_adj(xs[k], kick1[k] * gp, np_, nc, omega_m)
+        gx = gx + particle_force_adj(xs[k], kick1[k] * gp, np_, nc, omega_m, green, gradient)
     return gx, gp
 
 
