@@ -351,6 +351,50 @@ def measure_fwd_adjoint(wl, reps=1):
             "particle_steps_per_s_fwd_adj": wl.np_ ** 3 * wl.nsteps / (out["fwd_adj"] / 1e3)}
 
 
+def measure_force_variants(wl, reps=10):
+    """Cost of the force variants (naive / Eq. 4 Green's function x Eq. 5 /
+    exact gradient) at workload wl's mesh: CUDA-event ms of one fpm_force
+    (density -> three force meshes) and of one PM step inside a 5-step
+    fpm_kdk from 2LPT initial conditions."""
+    import numpy as np
+    import torch
+    from paper_2010_11847_gb300 import inputs
+    from paper_2010_11847_gb300.binding import Plan
+    pl = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    rho = torch.from_numpy((1.0 + 0.5 * inputs.random_field(wl.nc, 11)).astype(np.float32)).cuda()
+    F = torch.empty(3, wl.nc, wl.nc, wl.nc, device="cuda")
+    lk = pl.linear_field(torch.from_numpy(inputs.white_noise(wl.np_, wl.seed)).cuda())
+    stages = np.linspace(wl.a0, 1.0, 6)
+    dx0, p0 = pl.lpt(lk, float(stages[0]), 2)
+    out = {}
+    for green in ("naive", "discrete"):
+        for grad in ("fd4", "exact"):
+            pl.set_force_kernel(green, grad)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(3):
+                pl.force(rho, F)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                pl.force(rho, F)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_force = e0.elapsed_time(e1) / reps
+            dx, p = dx0.clone(), p0.clone()
+            pl.kdk(dx, p, stages)
+            dx, p = dx0.clone(), p0.clone()
+            torch.cuda.synchronize()
+            e0.record()
+            pl.kdk(dx, p, stages)
+            e1.record()
+            torch.cuda.synchronize()
+            assert pl.status() == 0
+            out[f"{green}/{grad}"] = {"ms_force": ms_force, "ms_per_pm_step": e0.elapsed_time(e1) / 5}
+    pl.set_force_kernel("naive", "fd4")
+    pl.close()
+    return {"workload": wl.name, "variants": out}
+
+
 def measure_reconstruction(iters=10, warmup=2):
     """Adam iterations of the Sec. 7.1 reconstruction (forward with checkpoints,
     adjoint, fused Adam + prior) at 128^3 particles on 128^3 cells, 400 Mpc/h,
@@ -530,6 +574,8 @@ def run_fpm(args):
         from paper_2010_11847_gb300 import inputs as _in
         extra["fwd_adjoint"] = measure_fwd_adjoint(wl)
         extra["reconstruction"] = measure_reconstruction()
+        torch.cuda.empty_cache()
+        extra["force_variants"] = measure_force_variants(wl)
         # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
         # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
         extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)

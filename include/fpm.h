@@ -110,9 +110,25 @@ int fpm_paint(fpm_plan* plan, const float* dx, float* rho,
 
 /* Force meshes from a density mesh (Eqs. 3-5):
  *   F_d = IDFT( i g_d(w) * 1.5 omega_m * DFT(rho - 1) / |w|^2 ),  F(0) = 0,
- * g_d(w) = (8 sin w_d - sin 2w_d)/6, w = 2 pi n / nc.  rho: float[nc^3];
- * F: float[3][nc^3]. */
+ * g_d(w) = (8 sin w_d - sin 2w_d)/6, w = 2 pi n / nc (the defaults of
+ * fpm_set_force_kernel).  rho: float[nc^3]; F: float[3][nc^3]. */
 int fpm_force(fpm_plan* plan, const float* rho, float* F, void* stream);
+
+/* Force kernel of the plan (Sec. 2): the Green's function and the gradient
+ * that fpm_force, fpm_kdk, the adjoint entry points and batches built from
+ * the plan use.  green: FPM_GREEN_NAIVE (default, |w|^2 = sum w_d^2) or
+ * FPM_GREEN_DISCRETE (Eq. 4, |w|^2 -> sum_d (2 sin(w_d/2))^2, the
+ * seven-point discrete Laplacian).  gradient: FPM_GRAD_FD4 (default, Eq. 5)
+ * or FPM_GRAD_EXACT (g_d = w_d, 0 at the Nyquist frequency).  The initial
+ * conditions (fpm_lpt) always use the defaults.  Synchronises the device
+ * (queued work may be reading the old tables).  Errors: FPM_EINVAL (null
+ * plan, unknown kind), FPM_ECUDA (table allocation or copy).
+ * fpm_batch_create returns FPM_ENOTIMPL for a plan with FPM_GRAD_EXACT. */
+#define FPM_GREEN_NAIVE 0
+#define FPM_GREEN_DISCRETE 1
+#define FPM_GRAD_FD4 0
+#define FPM_GRAD_EXACT 1
+int fpm_set_force_kernel(fpm_plan* plan, int green, int gradient);
 
 /* CIC readout of three meshes at the particles: f_out[d][i] =
  * sum_c W(q_i + dx_i - c) F[d][c].  F: float[3][nc^3]; f_out float[3][np^3]. */

@@ -41,6 +41,9 @@ struct fpm_plan {
   size_t N = 0, M = 0;
   FftTables tc, tp;            // mesh (nc) and lattice (np) tables
   bool share_tables = false;
+  FftTables tf;                // force tables of a non-default force kernel (else tc is used)
+  bool own_tf = false;
+  int green = FPM_GREEN_NAIVE, grad = FPM_GRAD_FD4;
   bool f4 = false;             // internal force meshes interleaved (float4 per cell)
   size_t specmax = 0;          // complex elements of one half spectrum
   float2* spec = nullptr;      // 6 half spectra
@@ -123,6 +126,7 @@ void free_plan(fpm_plan* p) {
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   if (p->tc.tw) fft_tables_destroy(&p->tc);
   if (!p->share_tables && p->tp.tw) fft_tables_destroy(&p->tp);
+  if (p->own_tf) fft_tables_destroy(&p->tf);
   delete p;
 }
 
@@ -172,10 +176,17 @@ int timed(fpm_plan* p, int cls, int nk, cudaStream_t s, Fn fn) {
   return rc;
 }
 
+// Tables of the plan's force kernel (Green's function and gradient symbols).
+const FftTables& force_tables(const fpm_plan* p) { return p->own_tf ? p->tf : p->tc; }
+
+// The potential form F_d = D_d phi needs the gradient to be Eq. 5's
+// real-space difference; the exact gradient takes the three-field path.
+bool force_via_potential(const fpm_plan* p) { return fft_has_potential(p->nc) && p->grad == FPM_GRAD_FD4; }
+
 int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s, bool interleaved = false) {
-  const FftTables& t = p->tc;
+  const FftTables& t = force_tables(p);
   const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
-  if (fft_has_potential(t.n)) {
+  if (force_via_potential(p)) {
     // phi = IFFT[coef delta / |w|^2] in the second half spectrum's memory,
     // then F_d = D_d phi (the Eq. 5 difference) in real space
     float* phi = reinterpret_cast<float*>(p->spec + p->specmax);
@@ -448,6 +459,29 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   });
 }
 
+int fpm_set_force_kernel(fpm_plan* p, int green, int gradient) {
+  if (!p || (green != FPM_GREEN_NAIVE && green != FPM_GREEN_DISCRETE) ||
+      (gradient != FPM_GRAD_FD4 && gradient != FPM_GRAD_EXACT))
+    return FPM_EINVAL;
+  if (green == p->green && gradient == p->grad) return FPM_OK;
+  FPM_CUDA_TRY(cudaDeviceSynchronize());
+  if (p->own_tf) fft_tables_destroy(&p->tf);
+  p->own_tf = false;
+  p->green = FPM_GREEN_NAIVE;
+  p->grad = FPM_GRAD_FD4;
+  if (green != FPM_GREEN_NAIVE || gradient != FPM_GRAD_FD4) {
+    const int rc = fft_tables_create(&p->tf, p->nc, green, gradient);
+    if (rc != FPM_OK) {
+      fft_tables_destroy(&p->tf);
+      return rc;
+    }
+    p->own_tf = true;
+  }
+  p->green = green;
+  p->grad = gradient;
+  return FPM_OK;
+}
+
 int fpm_power(fpm_plan* p, const float* a, const float* b, double* pk, double* kmean, double* nmodes,
               void* stream) {
   if (!p || !a) return FPM_EINVAL;
@@ -541,8 +575,8 @@ static int ensure_adjoint(fpm_plan* p) {
 
 // g_rho = -sum_d A_d g_F_d (A_d^T = -A_d for the real odd force kernels).
 static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream_t s) {
-  const FftTables& t = p->tc;
-  if (fft_has_potential(t.n)) {
+  const FftTables& t = force_tables(p);
+  if (force_via_potential(p)) {
     // F_d = D_d G rho with G symmetric and D^T = -D: g_rho = G (-sum_d D_d g_F_d)
     const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
     const int fused = t.n >= 128 ? 1 : 2;
@@ -767,7 +801,8 @@ int fpm_batch_create(fpm_batch** out, fpm_plan* const* plans, int nsims) {
     v.spec = p->spec;
     v.specmax = p->specmax;
     v.fac = p->d_fac;
-    v.tab = p->tc;
+    if (p->grad != FPM_GRAD_FD4) return FPM_ENOTIMPL;   // batched phases use the potential form
+    v.tab = force_tables(p);
     v.force_coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
   }
   fpm_batch* b = new fpm_batch();

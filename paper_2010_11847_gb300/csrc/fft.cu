@@ -8,7 +8,7 @@
 
 namespace fpm {
 
-int fft_tables_create(FftTables* t, int n) {
+int fft_tables_create(FftTables* t, int n, int green, int grad) {
   t->n = n;
   std::vector<float2> tw(n);
   std::vector<float> g(n), w2(n);
@@ -18,8 +18,10 @@ int fft_tables_create(FftTables* t, int n) {
     tw[m] = make_float2((float)cos(ang), (float)sin(ang));
     const int f = m < n / 2 ? m : m - n;            // signed frequency
     const double w = two_pi * f / n;
-    g[m] = (m == n / 2) ? 0.f : (float)((8.0 * sin(w) - sin(2.0 * w)) / 6.0);   // Eq. 5, 0 at Nyquist
-    w2[m] = (float)(w * w);
+    if (m == n / 2) g[m] = 0.f;                                   // 0 at Nyquist either way
+    else g[m] = grad ? (float)w : (float)((8.0 * sin(w) - sin(2.0 * w)) / 6.0);   // exact, or Eq. 5
+    const double s = 2.0 * sin(0.5 * w);                          // Eq. 4: w sinc(w/2)
+    w2[m] = (float)(green ? s * s : w * w);
   }
   FPM_CUDA_TRY(cudaMalloc(&t->tw, n * sizeof(float2)));
   FPM_CUDA_TRY(cudaMalloc(&t->g, n * sizeof(float)));

@@ -18,9 +18,9 @@ struct EhParams {
 struct FftTables {
   int n = 0;
   float2* tw = nullptr;    // exp(-2 pi i m / n), m = 0..n-1 (host FP64, rounded)
-  float* g = nullptr;      // Eq. 5 gradient (8 sin w - sin 2w)/6 of bin m, 0 at Nyquist
-  float* w2 = nullptr;     // (2 pi f / n)^2, f the signed frequency of bin m
-};
+  float* g = nullptr;      // gradient symbol of bin m, 0 at Nyquist: Eq. 5's (8 sin w - sin 2w)/6, or w
+  float* w2 = nullptr;     // Laplacian symbol of bin m: w^2 (naive), or (2 sin(w/2))^2 (Eq. 4)
+};                         // w = 2 pi f / n, f the signed frequency of bin m
 
 // Buffers of the sort + paint pipeline.
 struct PaintCtx {
@@ -46,7 +46,8 @@ int launch_factors(const double* d_pts, int nsteps, double om, double* d_raw, do
                    cudaStream_t s);
 
 // fft.cu
-int fft_tables_create(FftTables* t, int n);
+// green: 0 naive w^2, 1 Eq. 4 discrete; grad: 0 Eq. 5 difference, 1 exact w.
+int fft_tables_create(FftTables* t, int n, int green = 0, int grad = 0);
 void fft_tables_destroy(FftTables* t);
 int fft_zfwd(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
              cudaStream_t s);

@@ -35,4 +35,4 @@ class Reconstruction:
         self.t += 1
         prior = self.plan.adam_step(self.w, w.grad, self.m, self.v, self.t, lr=self.lr, betas=self.betas,
                                     eps=self.eps, gscale=0.5, pscale=1.0)
-        return 0.5 * float(chi2) + prior
+        return 0.5 * float(chi2.detach()) + prior
