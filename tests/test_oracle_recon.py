@@ -57,3 +57,29 @@ def test_posterior_gradient_by_central_differences(monkeypatch):
     fm, _ = O.posterior_and_grad(w - eps * u, target, nc, box, COSMO, stages)
     fd = (fp - fm) / (2 * eps)
     assert abs(fd - float((g * u).sum())) < 1e-6 * abs(fd)
+
+
+def test_white_noise_prior_is_the_fourier_space_prior(monkeypatch):
+    """Eq. 12's prior s^dagger S^-1 s / 2 written in Fourier space over the
+    linear field (S = P(k) N^3 / V per DFT mode, k != 0) plus the mean mode
+    of the white noise (which the data never see) equals the posterior's
+    prior term w^T w / 2 (Parseval over the half spectrum)."""
+    monkeypatch.setattr(O, "POSITIONS_FP32", False)
+    n, box = 8, 60.0
+    stages = np.linspace(0.1, 0.4, 2)
+    w = inputs.white_noise(n, 51).astype(np.float64)
+    target = inputs.random_field(n, 52).astype(np.float64) * 0.1
+    lin = O.linear_field(w, box, COSMO)
+    nx, ny, nz = O.half_spectrum_wavenumbers(n)
+    k = 2 * math.pi / box * np.sqrt((nx * nx + ny * ny + nz * nz).astype(np.float64))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        S = O.linear_pk(k, COSMO) * n ** 3 / box ** 3
+    mult = np.where((nz == 0) | (nz == n // 2), 1.0, 2.0) * np.ones_like(k)
+    ratio = np.zeros_like(k)
+    ratio[k > 0] = (np.abs(lin) ** 2)[k > 0] / S[k > 0]
+    fourier = float((mult * ratio).sum()) / n ** 3
+    mean_mode = float(w.sum()) ** 2 / n ** 3
+    post, gpost = O.posterior_and_grad(w, target, n, box, COSMO, stages)
+    chi2, gchi2 = O.chi2_and_grad(w, target, n, box, COSMO, stages)
+    assert abs((post - 0.5 * chi2) - 0.5 * (fourier + mean_mode)) < 1e-10 * post
+    np.testing.assert_allclose(gpost - 0.5 * gchi2, w, atol=1e-12)
