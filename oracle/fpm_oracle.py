@@ -506,22 +506,122 @@ def force(rho, omega_m, green="naive", gradient="fd4"):
     return force_from_delta(np.asarray(rho, dtype=np.float64) - 1.0, omega_m, green, gradient)
 
 
-def particle_force(dx, np_, nc, omega_m, green="naive", gradient="fd4"):
-    """paint -> force -> readout for particles at displacements dx."""
-    return readout(force(paint(dx, np_, nc), omega_m, green, gradient), dx, np_, nc)
+def particle_force(dx, np_, nc, omega_m, green="naive", gradient="fd4", pyramid=None):
+    """paint -> force -> readout for particles at displacements dx; with
+    ``pyramid`` (a dict of ``pyramid_force``'s levels, split, halo) the mesh
+    force is Algorithm 3's."""
+    rho = paint(dx, np_, nc)
+    F = pyramid_force(rho, omega_m, **pyramid) if pyramid else force(rho, omega_m, green, gradient)
+    return readout(F, dx, np_, nc)
+
+
+# ---------------------------------------------------------------------------
+# Multi-grid pyramid force (Sec. 3.1 Eqs. 6-9, Algorithms 2-3) on one device
+# ---------------------------------------------------------------------------
+def bspline_kernel(order=6):
+    """The order-`order` discrete B-spline: the box [1/2, 1/2] convolved
+    with itself `order` times, i.e. binomial weights C(order, j) / 2^order,
+    j = 0..order (7 taps for order 6), centred on tap order/2.  Its symbol
+    is cos(w/2)^order."""
+    k = np.array([1.0])
+    for _ in range(order):
+        k = np.convolve(k, [0.5, 0.5])
+    return k
+
+
+def _smooth_periodic(a, k):
+    """Periodic convolution of a 3-D field with the separable kernel k x k x k
+    (k symmetric, centred): out[x] = sum_j k[j] a[x + j - r] per axis."""
+    r = len(k) // 2
+    out = np.asarray(a, dtype=np.float64)
+    for ax in range(3):
+        out = sum(k[j] * np.roll(out, r - j, axis=ax) for j in range(len(k)))
+    return out
+
+
+def reduce_once(h, order=6):
+    """Eq. 6, g_{l+1} = S[G * g_l]: smooth with the 3-D B-spline, keep
+    every second node along each axis (a stride-2 convolution)."""
+    return _smooth_periodic(h, bspline_kernel(order))[::2, ::2, ::2]
+
+
+def expand_once(d, order=6):
+    """Eq. 7, g'_l = G * U[g_{l+1}]: insert zeros between the nodes and
+    smooth with 8 times the 3-D B-spline (Algorithm 2's EXPAND kernel), a
+    stride-2 transposed convolution."""
+    n = d.shape[0]
+    u = np.zeros((2 * n,) * 3)
+    u[::2, ::2, ::2] = d
+    return _smooth_periodic(u, 2.0 * bspline_kernel(order))
+
+
+def reduce(h, levels=2, order=6):
+    """Algorithm 2, REDUCE: `levels` stride-2 B-spline convolutions (two in
+    the paper's default, a mesh 4x coarser)."""
+    for _ in range(levels):
+        h = reduce_once(h, order)
+    return h
+
+
+def expand(d, levels=2, order=6):
+    """Algorithm 2, EXPAND: `levels` stride-2 transposed convolutions."""
+    for _ in range(levels):
+        d = expand_once(d, order)
+    return d
+
+
+def local_force(rho, omega_m, split, halo):
+    """The short-range force grids of Algorithm 3 computed with local FFTs:
+    the mesh is cut into split^3 cubic blocks of m = n/split cells; each block
+    is padded by `halo` cells of its periodic neighbours, its force computed
+    by ``force_from_delta`` as if the padded block were periodic (its own mean
+    removed), and its m^3 interior kept."""
+    rho = np.asarray(rho, dtype=np.float64)
+    n = rho.shape[0]
+    m = n // split
+    B = m + 2 * halo
+    F = np.zeros((3, n, n, n))
+    for bx in range(split):
+        for by in range(split):
+            for bz in range(split):
+                ix = [(np.arange(B) + b * m - halo) % n for b in (bx, by, bz)]
+                Fb = force_from_delta(rho[np.ix_(*ix)] - 1.0, omega_m)
+                inner = slice(halo, halo + m)
+                F[:, bx * m:(bx + 1) * m, by * m:(by + 1) * m, bz * m:(bz + 1) * m] = Fb[:, inner, inner, inner]
+    return F
+
+
+def pyramid_force(rho, omega_m, levels=2, split=2, halo=16, order=6):
+    """Algorithm 3: long-range force on the REDUCEd mesh (coarse cells are
+    2^levels fine cells, so the coarse force is multiplied by 2^levels to be
+    in fine-cell units), short-range force from local FFTs; the expanded
+    long-range force plus the short-range force minus its own band below the
+    coarse scale (EXPAND(REDUCE(F_S)))."""
+    rho = np.asarray(rho, dtype=np.float64)
+    D = reduce(rho - 1.0, levels, order)
+    FL = (2.0 ** levels) * force_from_delta(D, omega_m)
+    FS = local_force(rho, omega_m, split, halo)
+    F = np.empty_like(FS)
+    for i in range(3):
+        FLi = expand(FL[i], levels, order)
+        Fli = expand(reduce(FS[i], levels, order), levels, order)
+        F[i] = FLi + FS[i] - Fli
+    return F
 
 
 # ---------------------------------------------------------------------------
 # Time integration: KDK leapfrog (Eqs. 1-2)
 # ---------------------------------------------------------------------------
-def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None, green="naive", gradient="fd4"):
+def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None, green="naive", gradient="fd4",
+        pyramid=None):
     """Run len(stages)-1 KDK steps from (dx, p) at stages[0].
 
     The oracle performs the two half kicks of every step separately.  The
     particle-to-cell assignment uses the float32 value of dx (as the GPU
     stores it) when ``round_to_float32``; all arithmetic is FP64.
     ``record``, if a list, receives (dx, p) at the start of every step.
-    ``green`` and ``gradient`` select the force variant (``force_from_delta``).
+    ``green`` and ``gradient`` select the force variant (``force_from_delta``),
+    ``pyramid`` the multi-grid force (``pyramid_force``).
     """
     kick1, drift, kick2 = fastpm_factors(stages, omega_m)
     dx = np.array(dx, dtype=np.float64)
@@ -529,7 +629,7 @@ def kdk(dx, p, stages, np_, nc, omega_m, round_to_float32=True, record=None, gre
 
     def frc(x):
         xx = x.astype(np.float32) if round_to_float32 else x
-        return particle_force(xx, np_, nc, omega_m, green, gradient)
+        return particle_force(xx, np_, nc, omega_m, green, gradient, pyramid)
 
     f = frc(dx)
     for k in range(len(stages) - 1):
