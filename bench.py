@@ -395,6 +395,70 @@ def measure_force_variants(wl, reps=10):
     return {"workload": wl.name, "variants": out}
 
 
+def measure_pyramid(levels=2, split=2, halo=16):
+    """The multi-grid pyramid force (Algorithms 2-3) against the plain force
+    in the accuracy configuration (128^3 on 128^3, 400 Mpc/h, 10 KDK steps
+    from 1LPT at a = 0.1): residual of the final density contrast, transfer
+    function and cross-correlation of the two, and the cost of one force
+    evaluation (CUDA events) here and on the 512^3 mesh."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2010_11847_gb300 import inputs
+    from paper_2010_11847_gb300.binding import Plan
+    wl = inputs.ACCURACY_10STEP
+    pl = Plan(wl.np_, wl.nc, wl.box, wl.cosmo)
+    stages = wl.stages()
+    lk = pl.linear_field(torch.from_numpy(inputs.white_noise(wl.np_, wl.seed)).cuda())
+    dx0, p0 = pl.lpt(lk, float(stages[0]), 1)
+
+    def timed(fn, reps):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out, delta = {}, {}
+    for name, cfg in (("plain", (0, 0, 0)), ("pyramid", (levels, split, halo))):
+        pl.set_pyramid(*cfg)
+        dx, p = dx0.clone(), p0.clone()
+        pl.kdk(dx, p, stages)
+        delta[name] = pl.paint(dx) - 1.0
+        rho = delta[name] + 1.0
+        out[f"ms_force_{name}"] = timed(lambda: pl.force(rho), 10)
+        assert pl.status() == 0
+    dp, dm = delta["pyramid"], delta["plain"]
+    k, pa, _ = pl.power(dp)
+    _, pb, _ = pl.power(dm)
+    _, pab, _ = pl.power(dp, dm)
+    tf = np.sqrt(pa / pb)
+    rc = pab / np.sqrt(pa * pb)
+    low = k < 0.5 * math.pi * wl.nc / wl.box
+    out.update({"workload": wl.name, "levels": levels, "split": split, "halo": halo,
+                "block_mesh": wl.nc // split + 2 * halo, "coarse_mesh": wl.nc >> levels,
+                "field_residual_rms": float((dp - dm).pow(2).mean().sqrt() / dm.pow(2).mean().sqrt()),
+                "projected_residual_rms": float((dp - dm).sum(2).pow(2).mean().sqrt() / dm.sum(2).pow(2).mean().sqrt()),
+                "max_abs_tf_minus_1": float(np.abs(tf - 1).max()),
+                "max_abs_tf_minus_1_below_half_nyquist": float(np.abs(tf[low] - 1).max()),
+                "max_1_minus_rc": float((1 - rc).max()),
+                "max_1_minus_rc_below_half_nyquist": float((1 - rc[low]).max())})
+    pl.close()
+    big = inputs.LARGE
+    pb_ = Plan(128, big.nc, big.box, big.cosmo)
+    rho = torch.from_numpy((1.0 + 0.5 * inputs.random_field(big.nc, 12)).astype(np.float32)).cuda()
+    out["ms_force_plain_512"] = timed(lambda: pb_.force(rho), 5)
+    pb_.set_pyramid(2, 4, 32)
+    out["ms_force_pyramid_512"] = timed(lambda: pb_.force(rho), 5)
+    out["pyramid_512"] = {"levels": 2, "split": 4, "halo": 32, "block_mesh": 192, "coarse_mesh": 128}
+    pb_.close()
+    return out
+
+
 def measure_reconstruction(iters=10, warmup=2):
     """Adam iterations of the Sec. 7.1 reconstruction (forward with checkpoints,
     adjoint, fused Adam + prior) at 128^3 particles on 128^3 cells, 400 Mpc/h,
@@ -576,6 +640,8 @@ def run_fpm(args):
         extra["reconstruction"] = measure_reconstruction()
         torch.cuda.empty_cache()
         extra["force_variants"] = measure_force_variants(wl)
+        torch.cuda.empty_cache()
+        extra["pyramid"] = measure_pyramid()
         # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
         # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
         extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)

@@ -130,6 +130,23 @@ int fpm_force(fpm_plan* plan, const float* rho, float* F, void* stream);
 #define FPM_GRAD_EXACT 1
 int fpm_set_force_kernel(fpm_plan* plan, int green, int gradient);
 
+/* Multi-grid pyramid force (Sec. 3.1 Eqs. 6-9, Algorithms 2-3) for every
+ * later fpm_force / fpm_kdk of the plan; levels = 0 switches it off.
+ * F = EXPAND(F_L) + F_S - EXPAND(REDUCE(F_S)) with REDUCE = `levels`
+ * stride-2 convolutions with the order-6 discrete B-spline (binomial
+ * weights C(6, j)/64, periodic), EXPAND = the transposed convolutions with
+ * 8 times that kernel, F_L = 2^levels x the force of REDUCE(rho - 1) on the
+ * (nc >> levels)^3 mesh, F_S the force of local FFTs: split^3 cubic blocks
+ * of nc/split cells, each padded by `halo` cells of its periodic neighbours
+ * and transformed as a periodic mesh of B = nc/split + 2 halo cells, its
+ * interior kept.  Both meshes use the default kernel (naive Green's
+ * function, Eq. 5 gradient).  Requires levels in {1, 2}, nc >> levels and
+ * B among the FFT sizes (16, 32, 48, 64, 96, 128, 192, 256, 384, 512),
+ * split | nc.  Synchronises the device; allocates about 9 nc^3 floats.
+ * Errors: FPM_EINVAL, FPM_ENOMEM.  With a pyramid set, the adjoint entry
+ * points and fpm_batch_create return FPM_ENOTIMPL. */
+int fpm_set_pyramid(fpm_plan* plan, int levels, int split, int halo);
+
 /* CIC readout of three meshes at the particles: f_out[d][i] =
  * sum_c W(q_i + dx_i - c) F[d][c].  F: float[3][nc^3]; f_out float[3][np^3]. */
 int fpm_readout(fpm_plan* plan, const float* F, const float* dx, float* f_out,
@@ -305,7 +322,8 @@ int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream)
 #define FPM_K_POT_X 16    /* x pass with the Green's function (1 field)      */
 #define FPM_K_POT_INV 17  /* y inverse + z c2r to phi, one slab-ordered launch */
 #define FPM_K_POT_GRAD 18 /* Eq. 5 difference of phi to the force meshes     */
-#define FPM_K_COUNT 19
+#define FPM_K_PYRAMID 19  /* multi-grid pyramid force (Algorithm 3), all passes */
+#define FPM_K_COUNT 20
 
 /* Turn per-kernel-class timing on or off for this plan (off by default).
  * When on, every launch of the plan is bracketed by CUDA events recorded on

@@ -26,11 +26,11 @@ EXPORTS = [
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
     "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
     "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
-    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step", "fpm_set_force_kernel",
+    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step", "fpm_set_force_kernel", "fpm_set_pyramid",
 ]
 GREENS = {"naive": 0, "discrete": 1}     # FPM_GREEN_NAIVE, FPM_GREEN_DISCRETE (Eq. 4)
 GRADIENTS = {"fd4": 0, "exact": 1}       # FPM_GRAD_FD4 (Eq. 5), FPM_GRAD_EXACT
-FPM_K_COUNT = 19
+FPM_K_COUNT = 20
 
 
 class FpmError(RuntimeError):
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_chi2.argtypes = [vp, vp, vp, d, vp, vp, vp]
     L.fpm_adam_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64, d, d, d, d, d, d, ctypes.c_int, vp, vp]
     L.fpm_set_force_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.fpm_set_pyramid.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.fpm_paint_adj.argtypes = [vp, vp, vp, vp, vp]
     L.fpm_readout_adj.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_force_adj.argtypes = [vp, vp, vp, vp]
@@ -200,6 +201,11 @@ class Plan:
         """Green's function ("naive" or Eq. 4's "discrete") and gradient
         ("fd4", Eq. 5, or "exact") of every later force evaluation."""
         _check("fpm_set_force_kernel", lib().fpm_set_force_kernel(self._h, GREENS[green], GRADIENTS[gradient]))
+
+    def set_pyramid(self, levels=2, split=2, halo=16):
+        """Multi-grid pyramid force (Algorithm 3) for later force evaluations;
+        levels=0 switches it off."""
+        _check("fpm_set_pyramid", lib().fpm_set_pyramid(self._h, int(levels), int(split), int(halo)))
 
     def force(self, rho, F=None, stream=None):
         F = F if F is not None else self._empty(3, self.nc, self.nc, self.nc)

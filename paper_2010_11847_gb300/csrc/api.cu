@@ -44,6 +44,7 @@ struct fpm_plan {
   FftTables tf;                // force tables of a non-default force kernel (else tc is used)
   bool own_tf = false;
   int green = FPM_GREEN_NAIVE, grad = FPM_GRAD_FD4;
+  Pyramid* pyr = nullptr;      // multi-grid force (Algorithm 3) when set
   bool f4 = false;             // internal force meshes interleaved (float4 per cell)
   size_t specmax = 0;          // complex elements of one half spectrum
   float2* spec = nullptr;      // 6 half spectra
@@ -127,6 +128,10 @@ void free_plan(fpm_plan* p) {
   if (p->tc.tw) fft_tables_destroy(&p->tc);
   if (!p->share_tables && p->tp.tw) fft_tables_destroy(&p->tp);
   if (p->own_tf) fft_tables_destroy(&p->tf);
+  if (p->pyr) {
+    pyramid_destroy(p->pyr);
+    delete p->pyr;
+  }
   delete p;
 }
 
@@ -184,6 +189,13 @@ const FftTables& force_tables(const fpm_plan* p) { return p->own_tf ? p->tf : p-
 bool force_via_potential(const fpm_plan* p) { return fft_has_potential(p->nc) && p->grad == FPM_GRAD_FD4; }
 
 int force_impl(fpm_plan* p, const float* rho, float* F, cudaStream_t s, bool interleaved = false) {
+  if (p->pyr)
+    return timed(p, FPM_K_PYRAMID, 0, s, [&] {
+      int nl = 0;
+      const int rc = pyramid_force(*p->pyr, rho, F, interleaved, p->cosmo.omega_m, p->slab_ctr, p->d_err, s, &nl);
+      g_launches += nl;
+      return rc;
+    });
   const FftTables& t = force_tables(p);
   const float coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
   if (force_via_potential(p)) {
@@ -459,6 +471,32 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   });
 }
 
+int fpm_set_pyramid(fpm_plan* p, int levels, int split, int halo) {
+  if (!p || levels < 0) return FPM_EINVAL;
+  if (levels > 0) {
+    const int nco = levels <= 2 ? p->nc >> levels : 0;
+    if (levels > 2 || split < 1 || halo < 0 || p->nc % split != 0 || (nco << levels) != p->nc ||
+        !size_ok(nco) || !size_ok(p->nc / split + 2 * halo))
+      return FPM_EINVAL;
+  }
+  FPM_CUDA_TRY(cudaDeviceSynchronize());
+  if (p->pyr) {
+    pyramid_destroy(p->pyr);
+    delete p->pyr;
+    p->pyr = nullptr;
+  }
+  if (levels == 0) return FPM_OK;
+  Pyramid* y = new Pyramid();
+  const int rc = pyramid_create(y, p->nc, levels, split, halo);
+  if (rc != FPM_OK) {
+    pyramid_destroy(y);
+    delete y;
+    return rc == FPM_ECUDA ? FPM_ENOMEM : rc;
+  }
+  p->pyr = y;
+  return FPM_OK;
+}
+
 int fpm_set_force_kernel(fpm_plan* p, int green, int gradient) {
   if (!p || (green != FPM_GREEN_NAIVE && green != FPM_GREEN_DISCRETE) ||
       (gradient != FPM_GRAD_FD4 && gradient != FPM_GRAD_EXACT))
@@ -551,7 +589,7 @@ const char* fpm_kernel_class_name(int cls) {
                                            "fft_x_green", "fft_y_inv", "fft_z_c2r", "readout",
                                            "initial_conditions", "coefficients_fp64", "power_spectrum",
                                            "pot_fft_fwd_zy", "pot_fft_x_green", "pot_fft_inv_yz",
-                                           "pot_gradient"};
+                                           "pot_gradient", "pyramid_force"};
   return (cls >= 0 && cls < FPM_K_COUNT) ? names[cls] : "unknown";
 }
 
@@ -575,6 +613,7 @@ static int ensure_adjoint(fpm_plan* p) {
 
 // g_rho = -sum_d A_d g_F_d (A_d^T = -A_d for the real odd force kernels).
 static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream_t s) {
+  if (p->pyr) return FPM_ENOTIMPL;   // the pyramid force has no adjoint here
   const FftTables& t = force_tables(p);
   if (force_via_potential(p)) {
     // F_d = D_d G rho with G symmetric and D^T = -D: g_rho = G (-sum_d D_d g_F_d)
@@ -801,7 +840,7 @@ int fpm_batch_create(fpm_batch** out, fpm_plan* const* plans, int nsims) {
     v.spec = p->spec;
     v.specmax = p->specmax;
     v.fac = p->d_fac;
-    if (p->grad != FPM_GRAD_FD4) return FPM_ENOTIMPL;   // batched phases use the potential form
+    if (p->grad != FPM_GRAD_FD4 || p->pyr) return FPM_ENOTIMPL;   // batched phases use the potential form
     v.tab = force_tables(p);
     v.force_coef = (float)(1.5 * p->cosmo.omega_m / (double)p->M);
   }

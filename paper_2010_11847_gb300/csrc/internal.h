@@ -156,6 +156,30 @@ struct BatchPlanView {
 };
 struct Batch;
 bool batch_size_ok(int nc, int np);
+
+// Multi-grid pyramid force (pyramid.cu): coarse mesh nc >> levels, split^3
+// local blocks of nc/split cells padded by `halo` (B = nc/split + 2 halo).
+struct Pyramid {
+  int nc = 0, levels = 0, split = 0, halo = 0, nco = 0, m = 0, B = 0;
+  size_t spec_co = 0, spec_b = 0;   // complex elements of one coarse / block half spectrum
+  FftTables tco, tb;                // coarse and block FFT tables (default force kernel)
+  float* dco = nullptr;             // coarse density contrast, nco^3
+  float2* sco = nullptr;            // 3 coarse half spectra
+  float* FL = nullptr;              // coarse force [3][nco^3], then F_L - REDUCE(F_S)
+  float* blk = nullptr;             // padded block density, B^3
+  float2* sb = nullptr;             // 3 block half spectra
+  float* Fb = nullptr;              // block force [3][B^3]
+  float* FS = nullptr;              // short-range force [3][nc^3]
+  float* ping = nullptr;            // resampling scratch, 3 nc^3 / 2 each
+  float* pong = nullptr;
+  int64_t bytes = 0;
+};
+int pyramid_create(Pyramid* y, int nc, int levels, int split, int halo);
+void pyramid_destroy(Pyramid* y);
+// Force meshes of rho (mean 1) by Algorithm 3: planar F[3][nc^3] or float4
+// per cell (f4); `launches` is incremented by the kernels enqueued.
+int pyramid_force(const Pyramid& y, const float* rho, float* F, bool f4, double omega_m, unsigned* ctr, int* err,
+                  cudaStream_t s, int* launches);
 int batch_create(Batch** out, const BatchPlanView* views, int nsims);
 void batch_destroy(Batch* b);
 int batch_configure(Batch* b, int blocks_per_sm, int ro_iters, long long spin_limit);

@@ -50,6 +50,8 @@ LARGE = Workload("pm_512p_512m_1000mpc_40step", 512, 512, 1000.0, 40)
 # 1/8 of LARGE at the same cell size and particle density (profiling case)
 LARGE_EIGHTH = Workload("pm_256p_256m_500mpc_40step", 256, 256, 500.0, 40)
 DIFFERENTIABLE = Workload("pm_128p_128m_400mpc_5step_adjoint", 128, 128, 400.0, 5)
+# accuracy configuration of the mesh / pyramid comparison (1LPT initial conditions)
+ACCURACY_10STEP = Workload("pm_128p_128m_400mpc_10step_1lpt", 128, 128, 400.0, 10)
 
 
 def batched_workloads(seed0: int = 100) -> List[Workload]:
