@@ -27,14 +27,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Lines per block: the x pass keeps RegCfg's (64-byte rows at N = 512); the
-// z and y passes at N = 512 take 4 lines (256 threads), so that a block
-// barrier waits on fewer warps and more blocks interleave (measured faster).
+// Slots per thread and lines per block: the x pass keeps RegCfg's (8 slots,
+// 64-byte rows at N = 512).  At N = 512 the z and y passes give each thread
+// 16 slots (SLAB16: a line is one warp, its exchanges synchronise the warp
+// only) and take SLAB_L lines per block.
+constexpr bool SLAB16 = true;
+constexpr int SLAB_L = 4;
 template <int N, bool XP = false>
 struct PipeCfg {
-  static constexpr int T = RegCfg<N>::T;
-  static constexpr int L = (!XP && N == 512) ? 4 : RegCfg<N>::L;
+  static constexpr int V = (!XP && N == 512 && SLAB16) ? 16 : 8;
+  static constexpr int T = N / V;
+  static constexpr int L = (!XP && N == 512) ? SLAB_L : RegCfg<N>::L;
   static constexpr int THREADS = T * L;
+  static constexpr int MINB = V == 8 ? 1024 / THREADS : (640 / THREADS > 0 ? 640 / THREADS : 1);
   static constexpr int NH = N / 2 + 1;
   static constexpr int RL = N + 2;                  // line-major exchange (swizzled), 16-byte aligned
   static constexpr int RLX = N + N / 8 + (N == 128 ? 1 : 2);   // x pass exchange (padded)
@@ -95,15 +100,15 @@ __device__ __forceinline__ void comp_y(float2* base, int l0, int nlines, float2*
   constexpr int T = P::T;
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   float2* lb = buf + g * P::RL;
-  float2 v[8];
+  float2 v[P::V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = lb[t + T * s];
+  for (int s = 0; s < P::V; ++s) v[s] = lb[t + T * s];
   xsync<T>(1 + g);
-  RegFft<N>::template run<INV, 1>(v, lb, t, tw, 1 + g);
+  RegFft<N, P::V>::template run<INV, 1>(v, lb, t, tw, 1 + g);
   if (l0 + g < nlines) {
     float2* o = base + (size_t)(l0 + g) * N;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) o[t + T * s] = v[s];
+    for (int s = 0; s < P::V; ++s) o[t + T * s] = v[s];
   }
 }
 
@@ -113,14 +118,14 @@ __device__ __forceinline__ void comp_zf(float2* spec, size_t r0, float2* buf, co
   constexpr int T = P::T, L = P::L, NH = P::NH, RL = P::RL;
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   const float* rows = reinterpret_cast<const float*>(buf);
-  float2 v[8];
+  float2 v[P::V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = make_float2(rows[(2 * g) * N + t + T * s], rows[(2 * g + 1) * N + t + T * s]);
+  for (int s = 0; s < P::V; ++s) v[s] = make_float2(rows[(2 * g) * N + t + T * s], rows[(2 * g + 1) * N + t + T * s]);
   __syncthreads();                       // the exchange area overlaps other lines' rows
   float2* lb = buf + g * RL;
-  RegFft<N>::template run<false, 1>(v, lb, t, tw, 1 + g);
+  RegFft<N, P::V>::template run<false, 1>(v, lb, t, tw, 1 + g);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) lb[sw16(t + T * s)] = v[s];
+  for (int s = 0; s < P::V; ++s) lb[sw16(t + T * s)] = v[s];
   __syncthreads();
   const size_t x = r0 / N, y0 = r0 - x * N;
   for (int idx = threadIdx.x; idx < NH * L; idx += P::THREADS) {
@@ -166,14 +171,14 @@ __device__ __forceinline__ void comp_zi(float* phi, size_t r0, float2* buf, cons
   __syncthreads();
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   float2* lb = buf + g * RL;
-  float2 v[8];
+  float2 v[P::V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = lb[sw16(t + T * s)];
+  for (int s = 0; s < P::V; ++s) v[s] = lb[sw16(t + T * s)];
   xsync<T>(1 + g);
-  RegFft<N>::template run<true, 1>(v, lb, t, tw, 1 + g);
+  RegFft<N, P::V>::template run<true, 1>(v, lb, t, tw, 1 + g);
   float* dst = phi + (r0 + 2 * g) * N;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < P::V; ++s) {
     dst[t + T * s] = v[s].x;
     dst[N + t + T * s] = v[s].y;
   }
@@ -191,6 +196,7 @@ __device__ __forceinline__ void comp_x(float2* spec, int gl0, float coef, float2
   const int line = threadIdx.x % L, t = threadIdx.x / L;
   const int gl = gl0 + line;
   const int kz = gl / N, ky = gl - kz * N;
+  static_assert(P::V == 8, "the x pass keeps 8 slots");
   float2 d[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) d[s] = buf[(t + T * s) * L + line];

@@ -1,9 +1,10 @@
 // fft_reg.cuh -- register-resident Stockham FFT for power-of-two lengths
 // (internal), and the hot axis passes of the force step built on it.
 //
-// A line of N points is held by T = N/8 threads, thread t owning the
-// elements t + T*s, s = 0..7 (its 8 "slots").  A stage of radix R applies
-// 8/R butterflies per thread; butterfly j = t + T*q reads slots q + (8/R)*r,
+// A line of N points is held by T = N/V threads, thread t owning the
+// elements t + T*s, s = 0..V-1 (its V "slots"; V = 8, or 16 for one warp per
+// line at N = 512).  A stage of radix R applies V/R butterflies per thread;
+// butterfly j = t + T*q reads slots q + (V/R)*r,
 // so the inputs of every stage are in the thread's registers.  Between two
 // stages the outputs go through shared memory once (write at the Stockham
 // position (j/Ns)*Ns*R + j%Ns + r*Ns, barrier, read back t + T*s).  The
@@ -48,9 +49,9 @@ __device__ __forceinline__ void xsync(int sid) {
   }
 }
 
-template <int N, int R, int NS, bool INV, bool LAST, int LAY>
-__device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, const float2* tw, int sid) {
-  constexpr int T = N / 8, Q = 8 / R, TWS = N / (NS * R);
+template <int N, int V, int R, int NS, bool INV, bool LAST, int LAY>
+__device__ __forceinline__ void reg_stage(float2 (&v)[V], float2* buf, int t, const float2* tw, int sid) {
+  constexpr int T = N / V, Q = V / R, TWS = N / (NS * R);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + T * q;
@@ -79,36 +80,31 @@ __device__ __forceinline__ void reg_stage(float2 (&v)[8], float2* buf, int t, co
   if (!LAST) {
     xsync<T>(sid);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) v[s] = buf[xidx<LAY>(t + T * s)];
+    for (int s = 0; s < V; ++s) v[s] = buf[xidx<LAY>(t + T * s)];
     xsync<T>(sid);
   }
 }
 
-template <int N, bool INV, int LAY, int NS, int... Rs>
+template <int N, int V, bool INV, int LAY, int NS, int... Rs>
 struct RegStages;
-template <int N, bool INV, int LAY, int NS>
-struct RegStages<N, INV, LAY, NS> {
-  static __device__ __forceinline__ void run(float2 (&)[8], float2*, int, const float2*, int) {}
+template <int N, int V, bool INV, int LAY, int NS>
+struct RegStages<N, V, INV, LAY, NS> {
+  static __device__ __forceinline__ void run(float2 (&)[V], float2*, int, const float2*, int) {}
 };
-template <int N, bool INV, int LAY, int NS, int R, int... Rs>
-struct RegStages<N, INV, LAY, NS, R, Rs...> {
-  static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw, int sid) {
-    reg_stage<N, R, NS, INV, sizeof...(Rs) == 0, LAY>(v, buf, t, tw, sid);
-    RegStages<N, INV, LAY, NS * R, Rs...>::run(v, buf, t, tw, sid);
+template <int N, int V, bool INV, int LAY, int NS, int R, int... Rs>
+struct RegStages<N, V, INV, LAY, NS, R, Rs...> {
+  static __device__ __forceinline__ void run(float2 (&v)[V], float2* buf, int t, const float2* tw, int sid) {
+    reg_stage<N, V, R, NS, INV, sizeof...(Rs) == 0, LAY>(v, buf, t, tw, sid);
+    RegStages<N, V, INV, LAY, NS * R, Rs...>::run(v, buf, t, tw, sid);
   }
 };
 
-template <int N>
-struct RegFft;
+// Radix plan of each length (the same for V = 8 and 16).
+template <int N, int V, bool INV, int LAY>
+struct RegPlan;
 #define FPM_REG_PLAN(NN, ...)                                                                  \
-  template <>                                                                                  \
-  struct RegFft<NN> {                                                                          \
-    template <bool INV, int LAY = 0>                                                           \
-    static __device__ __forceinline__ void run(float2 (&v)[8], float2* buf, int t, const float2* tw, \
-                                               int sid = -1) {                                 \
-      RegStages<NN, INV, LAY, 1, __VA_ARGS__>::run(v, buf, t, tw, sid);                        \
-    }                                                                                          \
-  };
+  template <int V, bool INV, int LAY>                                                          \
+  struct RegPlan<NN, V, INV, LAY> : RegStages<NN, V, INV, LAY, 1, __VA_ARGS__> {};
 FPM_REG_PLAN(16, 8, 2)
 FPM_REG_PLAN(32, 8, 4)
 FPM_REG_PLAN(64, 8, 8)
@@ -116,6 +112,14 @@ FPM_REG_PLAN(128, 8, 8, 2)
 FPM_REG_PLAN(256, 8, 8, 4)
 FPM_REG_PLAN(512, 8, 8, 8)
 #undef FPM_REG_PLAN
+
+template <int N, int V = 8>
+struct RegFft {
+  template <bool INV, int LAY = 0>
+  static __device__ __forceinline__ void run(float2 (&v)[V], float2* buf, int t, const float2* tw, int sid = -1) {
+    RegPlan<N, V, INV, LAY>::run(v, buf, t, tw, sid);
+  }
+};
 
 __host__ __device__ constexpr bool is_pow2_size(int n) { return n >= 16 && n <= 512 && (n & (n - 1)) == 0; }
 
