@@ -31,6 +31,8 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // 64-byte rows at N = 512).  At N = 512 the z and y passes give each thread
 // 16 slots (SLAB16: a line is one warp, its exchanges synchronise the warp
 // only) and take SLAB_L lines per block.
+// (16 slots in the x pass, whose exchanges synchronise the block anyway,
+// measured slower: half the resident warps.)
 constexpr bool SLAB16 = true;
 constexpr int SLAB_L = 4;
 template <int N, bool XP = false>
@@ -39,7 +41,10 @@ struct PipeCfg {
   static constexpr int T = N / V;
   static constexpr int L = (!XP && N == 512) ? SLAB_L : RegCfg<N>::L;
   static constexpr int THREADS = T * L;
+  // resident blocks the launch bounds ask for: 16-slot passes get up to 102
+  // registers (5 blocks of 128), or 128 where the inverse pass would spill
   static constexpr int MINB = V == 8 ? 1024 / THREADS : (640 / THREADS > 0 ? 640 / THREADS : 1);
+  static constexpr int MINB_INV = V == 8 ? MINB : (512 / THREADS > 0 ? 512 / THREADS : 1);
   static constexpr int NH = N / 2 + 1;
   static constexpr int RL = N + 2;                  // line-major exchange (swizzled), 16-byte aligned
   static constexpr int RLX = N + N / 8 + (N == 128 ? 1 : 2);   // x pass exchange (padded)
@@ -196,22 +201,22 @@ __device__ __forceinline__ void comp_x(float2* spec, int gl0, float coef, float2
   const int line = threadIdx.x % L, t = threadIdx.x / L;
   const int gl = gl0 + line;
   const int kz = gl / N, ky = gl - kz * N;
-  static_assert(P::V == 8, "the x pass keeps 8 slots");
-  float2 d[8];
+  constexpr int V = P::V;
+  float2 d[V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) d[s] = buf[(t + T * s) * L + line];
+  for (int s = 0; s < V; ++s) d[s] = buf[(t + T * s) * L + line];
   __syncthreads();
   float2* lb = buf + line * P::RLX;
-  RegFft<N>::template run<false>(d, lb, t, tw);
+  RegFft<N, V>::template run<false>(d, lb, t, tw);
   const float w2yz = __ldg(g_w2 + ky) + __ldg(g_w2 + kz);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < V; ++s) {
     const float k2 = __ldg(g_w2 + t + T * s) + w2yz;
     d[s] = cscale(d[s], k2 > 0.f ? coef / k2 : 0.f);
   }
-  RegFft<N>::template run<true>(d, lb, t, tw);
+  RegFft<N, V>::template run<true>(d, lb, t, tw);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) spec[(size_t)(t + T * s) * S + gl] = d[s];
+  for (int s = 0; s < V; ++s) spec[(size_t)(t + T * s) * S + gl] = d[s];
 }
 
 }  // namespace fpm

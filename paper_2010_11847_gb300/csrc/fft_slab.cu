@@ -182,7 +182,8 @@ __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<
 }
 
 template <int N, int KIND>
-__global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS, PipeCfg<N, KIND == PK_X>::MINB)
+__global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS,
+                                  KIND == PK_INV ? PipeCfg<N>::MINB_INV : PipeCfg<N, KIND == PK_X>::MINB)
     k_pipe(PipeArgs a) {
   using P = PipeCfg<N, KIND == PK_X>;
   extern __shared__ __align__(16) float2 smem[];
