@@ -244,11 +244,12 @@ __device__ __forceinline__ void shell_decode(int s, int* l) {
 }
 
 // Deposit one warp's particles.  When the warp holds long runs of the same
-// local cell in adjacent lanes (at most 8 distinct runs: dense clumps, where
-// same-address atomics would serialise), each run is summed first
-// (segmented shuffle reduction; a run of <= 32 weights of <= 2^24 fits 32
-// bits) and its head lane adds the 8 corner sums; otherwise every lane adds
-// its own.
+// local cell in adjacent lanes (at most MERGE_RUNS distinct runs: dense
+// clumps, where same-address atomics would serialise), each run is summed
+// first (one redux.sync per corner over the run's lanes; a run of <= 32
+// weights of <= 2^24 fits 32 bits) and its head lane adds the 8 corner sums;
+// otherwise every lane adds its own.
+constexpr int MERGE_RUNS = 8;
 template <class A>
 __device__ __forceinline__ void deposit_warp(const A& acc, bool active, const int* l, const float* t) {
   const unsigned full = 0xffffffffu;
@@ -265,25 +266,20 @@ __device__ __forceinline__ void deposit_warp(const A& acc, bool active, const in
   const bool head = (lane == 0) || (prev != key);
   const unsigned heads = __ballot_sync(full, head);
   const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
-  if (__popc(heads) > 8) {
+  if (__popc(heads) > MERGE_RUNS) {
     if (active) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
     }
     return;
   }
+  // the lane's run is lanes [first, end): first = its head, end = next head
   const unsigned after = heads & ~((2u << lane) - 1u);
-  const int seg_end = after ? __ffs(after) - 1 : 32;
+  const int end = after ? __ffs(after) - 1 : 32;
+  const int first = 31 - __clz(heads & ((2u << lane) - 1u));
+  const unsigned run = (end == 32 ? full : ((1u << end) - 1u)) & ~((1u << first) - 1u);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    uint32_t s = w[c];
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t o = __shfl_down_sync(full, s, off);
-      if (lane + off < seg_end) s += o;
-    }
-    w[c] = s;
-  }
+  for (int c = 0; c < 8; ++c) w[c] = __reduce_add_sync(run, w[c]);
   if (active && head) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);

@@ -137,6 +137,30 @@ def test_paint_oversized_tile_path(torch_mod):
     np.testing.assert_array_equal(perm.cpu().numpy().view(np.uint32), O.sort_order(ref_keys))
 
 
+def test_paint_dense_clumps_hot_path(torch_mod):
+    """The hot-path paint (no permutation) with every particle in one of five
+    tight clumps: thousands of particles per cell, so warps hold long runs
+    of one cell (merged before the atomics) and the cell sums overflow the
+    low 32-bit word into its carry."""
+    torch = torch_mod
+    np_, nc = 32, 32
+    pl = make_plan(np_, nc)
+    rng = np.random.default_rng(15)
+    centres = np.array([[3, 4, 5], [3, 4, 6], [20, 9, 30], [31, 31, 31], [16, 0, 8]], dtype=np.float64)
+    pick = rng.integers(0, len(centres), size=np_ ** 3)
+    target = centres[pick].T + rng.uniform(0.0, 0.3, size=(3, np_ ** 3))
+    dx = (target - O.lattice(np_, nc)).astype(np.float32)
+    d = to_dev(dx, torch)
+    rho = pl.paint(d)
+    again = pl.paint(d)
+    torch.cuda.synchronize()
+    assert pl.status() == 0
+    assert torch.equal(rho, again)
+    ref = O.paint(dx, np_, nc)
+    assert ref.max() > 300.0                   # > 256 particles' worth of weight in a cell
+    assert rel_l2(rho.cpu().numpy(), ref) < 1e-5
+
+
 @pytest.mark.parametrize("np_,nc", [(32, 32), (32, 64), (64, 128)])
 def test_readout_matches_oracle(torch_mod, np_, nc):
     torch = torch_mod
