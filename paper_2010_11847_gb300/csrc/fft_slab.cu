@@ -12,10 +12,7 @@
 // queued before the second-phase items of slab s, and a second-phase item
 // waits (bounded) until all first-phase items of its slab are done.  A
 // slab's intermediate spectrum is then still in L2 when the second phase
-// reads it, so each pair of passes moves the data through HBM once.  After
-// the inverse z pass has read a slab's y-transformed spectrum, the consumed
-// 128-byte lines are dropped from L2 without write-back (discard.global.L2):
-// they are dead.
+// reads it, so each pair of passes moves the data through HBM once.
 //
 // Blocks claim items from a global counter in order, so an item only ever
 // waits on items claimed before it by running blocks.  A block claims and
@@ -96,21 +93,6 @@ __device__ __forceinline__ void slab_item(int item, int ns, int D, int nA, int n
   *ph = 1; *s = ns - D + r1 / nB; *j = r1 - (r1 / nB) * nB;
 }
 
-// Drop the 128-byte lines of the half spectrum that z item bx has read.
-template <int N>
-__device__ __forceinline__ void discard_z_item(const float2* spec, int bx) {
-  using P = PipeCfg<N>;
-  constexpr int NH = P::NH, LPR = (2 * P::L * 8) / 128;
-  if ((2 * P::L * 8) % 128 != 0) return;   // a line is shared with the next item: keep it
-  const size_t r0 = (size_t)bx * 2 * P::L;
-  const size_t x = r0 / N, y0 = r0 - x * N;
-  for (int e = threadIdx.x; e < NH * LPR; e += blockDim.x) {
-    const int kz = e / LPR, l = e - kz * LPR;
-    const float2* q = spec + (x * NH + kz) * N + y0 + 16 * l;
-    if (((uintptr_t)q & 127) == 0) asm volatile("discard.global.L2 [%0], 128;" ::"l"(q) : "memory");
-  }
-}
-
 enum PipeKind : int { PK_FWD = 0, PK_INV = 1, PK_X = 2 };
 
 // KIND PK_FWD: A = z r2c (ZF), B = y forward; PK_INV: A = y inverse, B = z
@@ -178,7 +160,6 @@ __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<
       atomicAdd(a.ctr + 1 + s, 1u);
     }
   }
-  if (KIND == PK_INV && ph == 1) discard_z_item<N>(a.spec, bx);
 }
 
 template <int N, int KIND>
