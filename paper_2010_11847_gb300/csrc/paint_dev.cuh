@@ -575,4 +575,5 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
   }
 }
 
+
 }  // namespace fpm
