@@ -169,10 +169,11 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(nsteps_target_s=12.0, max_steps=6):
-    """The FP64 oracle's PM step (paint, force, readout, kick, drift) on a
+def oracle_sample(steps=4, full_runs=True):
+    """The FP64 oracle's KDK steps (paint, force, readout, kick, drift) on a
     128^3-particle, 128^3-mesh sub-box of the 512^3 workload (same cell size
-    1000/512 Mpc/h and particle density), repeated for ~12 s."""
+    1000/512 Mpc/h and particle density): one continuous call over `steps`
+    steps (steps + 1 force evaluations), about 10 s of CPU work."""
     import numpy as np
     from oracle import fpm_oracle as O
     from paper_2010_11847_gb300 import inputs
@@ -182,21 +183,31 @@ def oracle_sample(nsteps_target_s=12.0, max_steps=6):
     lk = O.linear_field(inputs.white_noise(n, 7), box, wl.cosmo)
     dx, p = O.lpt(lk, n, wl.a0, wl.cosmo)
     stages = wl.stages()
-    times = []
-    t0 = time.perf_counter()
-    k = 0
-    while k < max_steps and (time.perf_counter() - t0) < nsteps_target_s:
-        t = time.perf_counter()
-        dx, p = O.kdk(dx, p, stages[k:k + 2], n, n, wl.cosmo["omega_m"])
-        times.append(time.perf_counter() - t)
-        k += 1
-    ms = 1e3 * statistics.median(times)
+    t = time.perf_counter()
+    O.kdk(dx, p, stages[:steps + 1], n, n, wl.cosmo["omega_m"])
+    ms = 1e3 * (time.perf_counter() - t) / steps
     threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
-    return {"value": n ** 3 / (ms / 1e3), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{k} KDK steps of the FP64 numpy/scipy oracle on a 128^3-particle 128^3-mesh "
-                      f"sub-box (250 Mpc/h, same cell size and density as 512^3/1000 Mpc/h); "
-                      f"median {ms:.0f} ms per step; scipy.fft may use all host cores",
-            "ms_per_pm_step": ms}
+    out = {"value": n ** 3 / (ms / 1e3), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{steps} KDK steps ({steps + 1} force evaluations) of the FP64 numpy/scipy oracle in one "
+                     f"call on a 128^3-particle 128^3-mesh sub-box (250 Mpc/h, same cell size and density as "
+                     f"512^3/1000 Mpc/h): {ms:.0f} ms per step; scipy.fft may use all host cores",
+           "ms_per_pm_step": ms}
+    if not full_runs:
+        return out
+    # the same sample, two steps, with one FFT thread (paint and readout are single-threaded anyway)
+    O.FFT_WORKERS = 1
+    t = time.perf_counter()
+    O.kdk(dx, p, stages[:3], n, n, wl.cosmo["omega_m"])
+    out["ms_per_pm_step_one_thread"] = 1e3 * (time.perf_counter() - t) / 2
+    O.FFT_WORKERS = -1
+    # whole simulations (linear field, 2LPT, all KDK steps, final paint) of the small configurations
+    runs = {}
+    for w in (inputs.SMALL, inputs.DIFFERENTIABLE):
+        t = time.perf_counter()
+        O.simulate(inputs.white_noise(w.np_, w.seed), w.nc, w.box, w.cosmo, w.stages())
+        runs[w.name] = {"ms_per_simulation": 1e3 * (time.perf_counter() - t), "kdk_steps": w.nsteps}
+    out["full_runs"] = runs
+    return out
 
 
 def run_reference(args):
@@ -212,12 +223,21 @@ def run_reference(args):
     lk = O.linear_field(inputs.white_noise(n, 7), box, wl.cosmo)
     dx, p = O.lpt(lk, n, wl.a0, wl.cosmo)
     stages = wl.stages()
-    for k in range(args.warmup):
-        dx, p = O.kdk(dx, p, stages[k:k + 2], n, n, wl.cosmo["omega_m"])
+    om = wl.cosmo["omega_m"]
+    # continuous KDK calls (a call of m steps evaluates m + 1 forces), at most
+    # the workload's 40 steps per call
+    w0 = min(args.warmup, wl.nsteps)
+    if w0:
+        dx, p = O.kdk(dx, p, stages[:w0 + 1], n, n, om)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        j = (args.warmup + k) % wl.nsteps
-        dx, p = O.kdk(dx, p, stages[j:j + 2], n, n, wl.cosmo["omega_m"])
+    done, j = 0, w0
+    while done < args.steps:
+        if j >= wl.nsteps:
+            j = 0
+        m = min(args.steps - done, wl.nsteps - j)
+        dx, p = O.kdk(dx, p, stages[j:j + m + 1], n, n, om)
+        done += m
+        j += m
     dt = time.perf_counter() - t0
     ms = 1e3 * dt / args.steps
     value = n ** 3 * args.steps / dt
@@ -226,9 +246,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "sample": "one oracle KDK step per bench step on a 128^3/128^3 "
-                       "sub-box at the 512^3 workload's resolution", "np": n, "nc": n, "box_mpc_h": box},
+                       "sub-box at the 512^3 workload's resolution, the timed steps in continuous calls",
+                       "np": n, "nc": n, "box_mpc_h": box},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "FP64 numpy/scipy oracle, 128^3 sub-box, one KDK step per bench step"},
+                             "sample": "FP64 numpy/scipy oracle, 128^3 sub-box, one KDK step per bench step "
+                                       "(continuous calls: a call of m steps evaluates m + 1 forces)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -459,6 +481,42 @@ def measure_pyramid(levels=2, split=2, halo=16):
     return out
 
 
+def measure_cufft_reference(reps=10):
+    """Reference only: cuFFT through torch.fft (rfftn + irfftn of one field)
+    at 512^3, against this library's forward + Green + inverse passes of the
+    potential (one field) from its own per-class CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2010_11847_gb300 import inputs
+    from paper_2010_11847_gb300.binding import Plan
+    n = inputs.LARGE.nc
+    rho = torch.from_numpy(inputs.random_field(n, 13)).cuda()
+    spec = torch.fft.rfftn(rho)
+    back = torch.fft.irfftn(spec, s=(n, n, n))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        spec = torch.fft.rfftn(rho)
+        back = torch.fft.irfftn(spec, s=(n, n, n))
+    e1.record()
+    torch.cuda.synchronize()
+    cufft = e0.elapsed_time(e1) / reps
+    del spec, back
+    pl = Plan(128, n, inputs.LARGE.box, inputs.LARGE.cosmo)
+    F = torch.empty(3, n, n, n, device="cuda")
+    pl.force(rho + 1.0, F)
+    pl.profile(True)
+    for _ in range(reps):
+        pl.force(rho + 1.0, F)
+    prof = pl.profile_read()
+    pl.profile(False)
+    pl.close()
+    ours = sum(prof[k][0] for k in ("pot_fft_fwd_zy", "pot_fft_x_green", "pot_fft_inv_yz") if k in prof) / reps
+    return {"mesh": n, "ms_cufft_rfftn_plus_irfftn": cufft, "ms_ours_fwd_green_inv": ours,
+            "note": "reference only: cuFFT is a library transform pair without the Green's function"}
+
+
 def measure_reconstruction(iters=10, warmup=2):
     """Adam iterations of the Sec. 7.1 reconstruction (forward with checkpoints,
     adjoint, fused Adam + prior) at 128^3 particles on 128^3 cells, 400 Mpc/h,
@@ -642,6 +700,8 @@ def run_fpm(args):
         extra["force_variants"] = measure_force_variants(wl)
         torch.cuda.empty_cache()
         extra["pyramid"] = measure_pyramid()
+        torch.cuda.empty_cache()
+        extra["cufft_reference"] = measure_cufft_reference()
         # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
         # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
         extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)

@@ -30,14 +30,16 @@ import math
 
 import numpy as np
 
+FFT_WORKERS = -1   # threads of the library FFT (-1: all host cores)
+
 try:                                     # multithreaded pocketfft if present
     import scipy.fft as _fft
 
     def _rfftn(a):
-        return _fft.rfftn(a, workers=-1)
+        return _fft.rfftn(a, workers=FFT_WORKERS)
 
     def _irfftn(a, n):
-        return _fft.irfftn(a, s=(n, n, n), workers=-1)
+        return _fft.irfftn(a, s=(n, n, n), workers=FFT_WORKERS)
 except ImportError:                      # pragma: no cover
     def _rfftn(a):
         return np.fft.rfftn(a)
