@@ -103,6 +103,7 @@ void free_plan(fpm_plan* p) {
   cudaFree(p->slab_ctr);
   cudaFree(p->pc.keys);
   cudaFree(p->pc.items);
+  cudaFree(p->pc.cells);
   cudaFree(p->pc.tile_count);
   cudaFree(p->pc.tile_start);
   cudaFree(p->pc.tile_cursor);
@@ -306,6 +307,7 @@ int fpm_plan_create(fpm_plan** out, int np, int nc, double box, const fpm_cosmo*
   c.ntiles = c.g.nt * c.g.nt * c.g.nt;
   TRY(dalloc(p, &c.keys, p->N));
   TRY(dalloc(p, &c.items, p->N));
+  TRY(dalloc(p, &c.cells, p->N));
   TRY(dalloc(p, &c.tile_count, (size_t)c.ntiles));
   TRY(dalloc(p, &c.tile_start, (size_t)c.ntiles + 1));
   TRY(dalloc(p, &c.tile_cursor, (size_t)c.ntiles));

@@ -29,6 +29,8 @@ struct PaintCtx {
   int ntiles = 0;
   uint32_t* keys = nullptr;        // [N]
   uint32_t* items = nullptr;       // [N] particle indices bucketed by tile
+  uint16_t* cells = nullptr;       // [N] in-tile cell (key & 4095) of each item, written with the
+                                   // cube bucketing; null: the paint recomputes it from dx
   uint32_t* tile_count = nullptr;  // [ntiles]
   uint32_t* tile_start = nullptr;  // [ntiles + 1]
   uint32_t* tile_cursor = nullptr; // [ntiles]

@@ -56,6 +56,8 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ke
 // integer sums and the stable sort of the permutation output do not depend
 // on it).
 constexpr int SC_THREADS = 512;
+// The cube bucketing also records each item's in-tile cell for the paint.
+constexpr bool PAINT_CELLS = true;
 constexpr int SC_CUBE = 16;
 constexpr int SC_PER = SC_CUBE * SC_CUBE * SC_CUBE / SC_THREADS;   // 8
 constexpr int SC_TBL = 256;
@@ -68,15 +70,16 @@ __device__ __forceinline__ uint32_t cube_index(int e, int t, int cx, int cy, int
 
 __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                              uint32_t* __restrict__ cursor,
-                                                             uint32_t* __restrict__ items) {
+                                                             uint32_t* __restrict__ items,
+                                                             uint16_t* __restrict__ cells) {
   __shared__ uint32_t t_tile[SC_TBL], t_cnt[SC_TBL], t_base[SC_TBL];
   const unsigned full = 0xffffffffu;
   const int t = threadIdx.x, lane = t & 31;
   const int ncube = np / SC_CUBE;
   const int cz = blockIdx.x % ncube, cy = (blockIdx.x / ncube) % ncube, cx = blockIdx.x / (ncube * ncube);
-  uint32_t tile[SC_PER];
+  uint32_t key[SC_PER];
 #pragma unroll
-  for (int e = 0; e < SC_PER; ++e) tile[e] = __ldcg(keys + cube_index(e, t, cx, cy, cz, np)) >> 12;
+  for (int e = 0; e < SC_PER; ++e) key[e] = __ldcg(keys + cube_index(e, t, cx, cy, cz, np));
   for (int k = t; k < SC_TBL; k += SC_THREADS) {
     t_tile[k] = 0xffffffffu;
     t_cnt[k] = 0;
@@ -85,26 +88,28 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* 
   uint32_t packed[SC_PER];   // slot << 16 | place in the cube's range; ~0 once written directly
 #pragma unroll
   for (int e = 0; e < SC_PER; ++e) {
-    const unsigned grp = __match_any_sync(full, tile[e]);
+    const uint32_t tile = key[e] >> 12;
+    const unsigned grp = __match_any_sync(full, tile);
     const int leader = __ffs(grp) - 1;
     int sl = -1;
     uint32_t off = 0;
     if (lane == leader) {
-      uint32_t h = (tile[e] * 2654435761u) >> 24;
+      uint32_t h = (tile * 2654435761u) >> 24;
       for (int probe = 0; probe < SC_TBL; ++probe, h = (h + 1) & (SC_TBL - 1)) {
-        const uint32_t prev = atomicCAS(&t_tile[h], 0xffffffffu, tile[e]);
-        if (prev == 0xffffffffu || prev == tile[e]) {
+        const uint32_t prev = atomicCAS(&t_tile[h], 0xffffffffu, tile);
+        if (prev == 0xffffffffu || prev == tile) {
           sl = (int)h;
           break;
         }
       }
       off = sl >= 0 ? atomicAdd(&t_cnt[sl], (uint32_t)__popc(grp))
-                    : atomicAdd(cursor + tile[e], (uint32_t)__popc(grp));   // table full: direct
+                    : atomicAdd(cursor + tile, (uint32_t)__popc(grp));   // table full: direct
     }
     sl = __shfl_sync(full, sl, leader);
     const uint32_t place = __shfl_sync(full, off, leader) + __popc(grp & ((1u << lane) - 1u));
     if (sl < 0) {
       items[place] = cube_index(e, t, cx, cy, cz, np);
+      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
       packed[e] = 0xffffffffu;
     } else {
       packed[e] = ((uint32_t)sl << 16) | place;
@@ -116,7 +121,11 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* 
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < SC_PER; ++e)
-    if (packed[e] != 0xffffffffu) items[t_base[packed[e] >> 16] + (packed[e] & 0xffffu)] = cube_index(e, t, cx, cy, cz, np);
+    if (packed[e] != 0xffffffffu) {
+      const uint32_t place = t_base[packed[e] >> 16] + (packed[e] & 0xffffu);
+      items[place] = cube_index(e, t, cx, cy, cz, np);
+      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
+    }
 }
 
 __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,
@@ -135,10 +144,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket_faces(const float* 
                                                                    const uint32_t* __restrict__ tile_start, Geom g,
                                                                    float* __restrict__ rho,
                                                                    unsigned long long* __restrict__ halo,
-                                                                   uint32_t* __restrict__ done, int* __restrict__ err) {
+                                                                   uint32_t* __restrict__ done, int* __restrict__ err,
+                                                                   const uint16_t* __restrict__ cells) {
   __shared__ uint32_t lo[ACC], hi[ACC];
   __shared__ uint32_t sm[24];
-  body_paint_bucket(dx, N, items, tile_start, g, rho, halo, err, lo, hi, blockIdx.x);
+  body_paint_bucket_acc<false>(dx, N, items, tile_start, g, rho, halo, err, Acc32{lo, hi}, blockIdx.x, cells);
   paint_faces_last(done, halo, g, rho, blockIdx.x, sm);
 }
 
@@ -338,7 +348,8 @@ int launch_scan(const PaintCtx& c, cudaStream_t s) {
 int launch_scatter(const PaintCtx& c, cudaStream_t s) {
   if (c.g.np % SC_CUBE == 0) {
     const int nq = c.g.np / SC_CUBE;
-    k_scatter_cube<<<nq * nq * nq, SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor, c.items);
+    k_scatter_cube<<<nq * nq * nq, SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor, c.items,
+                                                       PAINT_CELLS ? c.cells : nullptr);
   } else {
     k_scatter<<<grid_of(c.N, 256 * SCAT_E), 256, 0, s>>>(c.keys, c.N, c.tile_cursor, c.items);
   }
@@ -352,7 +363,7 @@ int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t*
                                                               c.halo, perm, c.err);
   } else if (c.tile_done) {
     k_paint_bucket_faces<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo,
-                                                          c.tile_done, c.err);
+                                                          c.tile_done, c.err, PAINT_CELLS ? c.cells : nullptr);
   } else {
     k_paint_bucket<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo, c.err);
   }

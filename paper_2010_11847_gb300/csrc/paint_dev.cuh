@@ -358,7 +358,8 @@ __device__ __forceinline__ void body_paint_bucket_acc(const float* __restrict__ 
                                                       const uint32_t* __restrict__ items,
                                                       const uint32_t* __restrict__ tile_start, Geom g,
                                                       float* __restrict__ rho, unsigned long long* __restrict__ halo,
-                                                      int* __restrict__ err, const A& acc, int bx) {
+                                                      int* __restrict__ err, const A& acc, int bx,
+                                                      const uint16_t* __restrict__ cells = nullptr) {
   const int nt = g.nt;
   const int tile = bx;
   const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
@@ -372,7 +373,23 @@ __device__ __forceinline__ void body_paint_bucket_acc(const float* __restrict__ 
     const bool active = k < n;
     int l[3] = {0, 0, 0};
     float t[3] = {0.f, 0.f, 0.f};
-    if (active) bad |= !particle_local<COH>(dx, N, ld_part<COH>(items + s0 + k), g, o, l, t);
+    if (active) {
+      const uint32_t i = ld_part<COH>(items + s0 + k);
+      if (cells) {
+        // in-tile cell from the bucketing (the key's low 12 bits), fraction from dx
+        const uint32_t lc = ld_part<COH>(cells + s0 + k);
+        l[0] = (int)(lc >> 8);
+        l[1] = (int)(lc >> 4) & (TILE - 1);
+        l[2] = (int)lc & (TILE - 1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float d = ld_part<COH>(dx + a * N + i);
+          t[a] = d - floorf(d);
+        }
+      } else {
+        bad |= !particle_local<COH>(dx, N, i, g, o, l, t);
+      }
+    }
     deposit_warp(acc, active, l, t);
   }
   if (bad) atomicOr(err, ERR_RANGE);
