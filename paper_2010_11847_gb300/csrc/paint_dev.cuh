@@ -212,6 +212,7 @@ struct Acc32 {
   __device__ __forceinline__ unsigned long long get(int c) const { return acc_get(lo, hi, c); }
   __device__ __forceinline__ void zero(int c) const { lo[c] = hi[c] = 0u; }
 };
+
 __device__ __forceinline__ int shell_index(int lx, int ly, int lz) {
   // cells of the 17^3 block with a coordinate in {0, 16}
   if (lx == 0 || lx == TILE) return (lx == TILE) * TILE1 * TILE1 + ly * TILE1 + lz;
