@@ -644,7 +644,8 @@ static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream
 // gx += J_f(x)^T v at the positions x whose paint (buckets) and force
 // meshes (p->F, interleaved when p->f4) are current; uses p->rho as scratch.
 static int force_jt_impl(fpm_plan* p, const float* x, const float* v, float* gx, cudaStream_t s) {
-  FPM_TRY(timed(p, FPM_K_PAINT, 7, s, [&] { return launch_paint_vec(p->pc, x, v, p->vmax, p->gF, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, p->pc.tile_done ? 4 : 7, s,
+                [&] { return launch_paint_vec(p->pc, x, v, p->vmax, p->gF, s); }));
   FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
   return timed(p, FPM_K_READOUT, 1, s,
                [&] { return launch_gather_adj(p->pc, x, p->rho, p->F, p->f4, v, gx, true, s); });
@@ -702,7 +703,7 @@ int fpm_readout_adj(fpm_plan* p, const float* F, const float* dx, const float* g
   FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, dx, s); }));
   FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
   FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
-  FPM_TRY(timed(p, FPM_K_PAINT, 7, s, [&] { return launch_paint_vec(c, dx, g_f, p->vmax, g_F, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s, [&] { return launch_paint_vec(c, dx, g_f, p->vmax, g_F, s); }));
   return timed(p, FPM_K_READOUT, 1, s,
                [&] { return launch_gather_adj(c, dx, nullptr, F, false, g_f, g_dx, false, s); });
 }

@@ -56,11 +56,16 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ ke
 // integer sums and the stable sort of the permutation output do not depend
 // on it).
 constexpr int SC_THREADS = 512;
-// The cube bucketing also records each item's in-tile cell for the paint.
+// The cube bucketing also records each item's in-tile cell for the paints.
 constexpr bool PAINT_CELLS = true;
 constexpr int SC_CUBE = 16;
 constexpr int SC_PER = SC_CUBE * SC_CUBE * SC_CUBE / SC_THREADS;   // 8
 constexpr int SC_TBL = 256;
+
+// In-tile cells recorded by the cube bucketing (null where it did not run).
+inline uint16_t* cells_of(const PaintCtx& c) {
+  return (PAINT_CELLS && c.g.np % SC_CUBE == 0) ? c.cells : nullptr;
+}
 
 __device__ __forceinline__ uint32_t cube_index(int e, int t, int cx, int cy, int cz, int np) {
   const int l = e * SC_THREADS + t;
@@ -348,8 +353,7 @@ int launch_scan(const PaintCtx& c, cudaStream_t s) {
 int launch_scatter(const PaintCtx& c, cudaStream_t s) {
   if (c.g.np % SC_CUBE == 0) {
     const int nq = c.g.np / SC_CUBE;
-    k_scatter_cube<<<nq * nq * nq, SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor, c.items,
-                                                       PAINT_CELLS ? c.cells : nullptr);
+    k_scatter_cube<<<nq * nq * nq, SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor, c.items, cells_of(c));
   } else {
     k_scatter<<<grid_of(c.N, 256 * SCAT_E), 256, 0, s>>>(c.keys, c.N, c.tile_cursor, c.items);
   }
@@ -363,7 +367,7 @@ int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t*
                                                               c.halo, perm, c.err);
   } else if (c.tile_done) {
     k_paint_bucket_faces<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo,
-                                                          c.tile_done, c.err, PAINT_CELLS ? c.cells : nullptr);
+                                                          c.tile_done, c.err, cells_of(c));
   } else {
     k_paint_bucket<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, rho, c.halo, c.err);
   }
@@ -464,12 +468,14 @@ __global__ void k_maxabs(const float* __restrict__ v, size_t n, unsigned* __rest
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// Fixed-point unit 2^S for signed deposits: |w v| 2^S <= 2^30 for every
-// deposit (weights <= 1), a power of two so scaling is exact.
+// Fixed-point unit 2^S for signed deposits: |w v| 2^S < 2^29 for every
+// deposit (weights <= 1), built from the exponent bits of max |v| so that it
+// is exactly a power of two.
 __device__ __forceinline__ float signed_scale(unsigned maxbits) {
-  const float m = __uint_as_float(maxbits);
-  if (!(m > 0.f)) return 1.f;
-  return exp2f(floorf(30.f - log2f(m)) - 1.f);
+  // m < 2^(e+1) with e the unbiased exponent of m: S = 28 - e gives m 2^S < 2^29
+  const int e = (int)((maxbits >> 23) & 0xffu) - 127;
+  if (maxbits == 0u || e < -100 || e > 100) return 1.f;
+  return __int_as_float((127 + 28 - e) << 23);
 }
 
 // 64-bit two's-complement accumulation of a signed 32-bit value with 32-bit
@@ -484,6 +490,33 @@ __device__ __forceinline__ float from_fix_signed(long long v, float inv_scale) {
   return __ll2float_rn(v) * inv_scale;     // one rounding of the exact sum; the scale is a power of two
 }
 
+// Face cells of tile bx from the shells of the up to 8 tiles covering them
+// (signed fixed point, unit 1/inv); nb: 8 words of shared memory.
+__device__ __forceinline__ void body_halo_vec(const unsigned long long* __restrict__ halo, const Geom& g, float inv,
+                                              float* __restrict__ out, uint32_t* nb, int bx) {
+  const int nt = g.nt, nc = g.nc;
+  const int tc[3] = {bx / (nt * nt), (bx / nt) % nt, bx % nt};
+  if (threadIdx.x < 8) {
+    const int b = threadIdx.x;
+    const int x = tc[0] - (b >> 2), y = tc[1] - ((b >> 1) & 1), z = tc[2] - (b & 1);
+    nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NFACE; k += blockDim.x) {
+    int l[3];
+    face_cell(k, l);
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int ox = b >> 2, oy = (b >> 1) & 1, oz = b & 1;
+      if ((ox && l[0]) || (oy && l[1]) || (oz && l[2])) continue;
+      sum += __ldcg(halo + (size_t)nb[b] * SHELL + shell_index(l[0] + TILE * ox, l[1] + TILE * oy, l[2] + TILE * oz));
+    }
+    out[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
+        from_fix_signed((long long)sum, inv);
+  }
+}
+
 // Readout transpose for one channel: out_c = sum_i W(x_i - c) v_i (no
 // mass), deterministic signed fixed point in units set by max |v|.
 __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restrict__ dx, size_t N,
@@ -492,8 +525,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
                                                           const float* __restrict__ vch,
                                                           const unsigned* __restrict__ vmax,
                                                           float* __restrict__ out,
-                                                          unsigned long long* __restrict__ halo) {
+                                                          unsigned long long* __restrict__ halo,
+                                                          const uint16_t* __restrict__ cells,
+                                                          uint32_t* __restrict__ done) {
   __shared__ uint32_t lo[ACC], hi[ACC];
+  __shared__ uint32_t sm[24];
   const int nt = g.nt, nc = g.nc;
   const int tile = blockIdx.x;
   const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
@@ -505,7 +541,19 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
     const uint32_t i = __ldg(items + k);
     int l[3];
     float t[3];
-    if (!particle_local<false>(dx, N, i, g, o, l, t)) continue;
+    if (cells) {
+      const uint32_t lc = __ldg(cells + k);
+      l[0] = (int)(lc >> 8);
+      l[1] = (int)(lc >> 4) & (TILE - 1);
+      l[2] = (int)lc & (TILE - 1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float d = __ldg(dx + a * N + i);
+        t[a] = d - floorf(d);
+      }
+    } else if (!particle_local<false>(dx, N, i, g, o, l, t)) {
+      continue;
+    }
     const float vs = __ldg(vch + i) * scale;
     const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
@@ -526,6 +574,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
     shell_decode(s, l);
     hb[s] = acc_get(lo, hi, (l[0] * TILE1 + l[1]) * TILE1 + l[2]);
   }
+  if (done) faces_last(done, halo, g, tile, sm, [&](int u) { body_halo_vec(halo, g, inv, out, sm, u); });
 }
 
 // Face cells of the vector paint: signed sums of the covering tiles' shells.
@@ -582,10 +631,12 @@ int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigne
   FPM_CUDA_TRY(cudaGetLastError());
   for (int ch = 0; ch < 3; ++ch) {
     k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vmax,
-                                                out + ch * c.M, c.halo);
+                                                out + ch * c.M, c.halo, cells_of(c), c.tile_done);
     FPM_CUDA_TRY(cudaGetLastError());
-    k_halo_vec<<<c.ntiles, 768, 0, s>>>(c.halo, c.g, vmax, out + ch * c.M);
-    FPM_CUDA_TRY(cudaGetLastError());
+    if (!c.tile_done) {
+      k_halo_vec<<<c.ntiles, 768, 0, s>>>(c.halo, c.g, vmax, out + ch * c.M);
+      FPM_CUDA_TRY(cudaGetLastError());
+    }
   }
   return FPM_OK;
 }

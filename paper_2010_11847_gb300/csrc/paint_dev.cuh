@@ -410,6 +410,26 @@ __device__ __forceinline__ void body_paint_bucket(const float* __restrict__ dx, 
 // Lower-face cells of every tile: sum the shell partials of the up to 8
 // tiles whose 17^3 blocks cover the cell.  One thread per face cell.
 // nb: 8 words of shared memory.
+// In-tile coordinates of lower-face cell k < NFACE: the x = 0 face, then
+// y = 0 (x >= 1), then z = 0 (x, y >= 1).
+__device__ __forceinline__ void face_cell(int k, int* l) {
+  if (k < TILE * TILE) {
+    l[0] = 0;
+    l[1] = k >> 4;
+    l[2] = k & 15;
+  } else if (k < TILE * TILE + (TILE - 1) * TILE) {
+    const int r = k - TILE * TILE;
+    l[0] = 1 + (r >> 4);
+    l[1] = 0;
+    l[2] = r & 15;
+  } else {
+    const int r = k - TILE * TILE - (TILE - 1) * TILE;
+    l[0] = 1 + r / (TILE - 1);
+    l[1] = 1 + r % (TILE - 1);
+    l[2] = 0;
+  }
+}
+
 __device__ __forceinline__ void body_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
                                                 float* __restrict__ rho, uint32_t* nb, int bx) {
   const int nt = g.nt, nc = g.nc;
@@ -423,21 +443,7 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
   __syncthreads();
   for (int k = threadIdx.x; k < NFACE; k += blockDim.x) {
     int l[3];
-    if (k < TILE * TILE) {
-      l[0] = 0;
-      l[1] = k >> 4;
-      l[2] = k & 15;
-    } else if (k < TILE * TILE + (TILE - 1) * TILE) {
-      const int r = k - TILE * TILE;
-      l[0] = 1 + (r >> 4);
-      l[1] = 0;
-      l[2] = r & 15;
-    } else {
-      const int r = k - TILE * TILE - (TILE - 1) * TILE;
-      l[0] = 1 + r / (TILE - 1);
-      l[1] = 1 + r % (TILE - 1);
-      l[2] = 0;
-    }
+    face_cell(k, l);
     unsigned long long sum = 0;
   #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -459,11 +465,11 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
 // barrier, fence, count; acquire: count seen at 7, fence, block barrier.
 // The finisher resets the count for the next paint.  sm: 24 words of
 // shared memory.
-__device__ __forceinline__ void paint_faces_last(uint32_t* __restrict__ done, const unsigned long long* halo,
-                                                 const Geom& g, float* __restrict__ rho, int tile, uint32_t* sm) {
+template <class Fn>
+__device__ __forceinline__ void faces_last(uint32_t* __restrict__ done, const unsigned long long* halo,
+                                           const Geom& g, int tile, uint32_t* sm, Fn sum_faces) {
   const int nt = g.nt;
-  uint32_t* nb = sm;                 // 8 words: neighbour tiles of the face sum
-  uint32_t* list = sm + 8;           // up to 8 completed tiles
+  uint32_t* list = sm + 8;           // up to 8 completed tiles (sm[0..7]: the face sum's neighbours)
   __syncthreads();
   if (threadIdx.x == 0) {
     const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
@@ -481,10 +487,15 @@ __device__ __forceinline__ void paint_faces_last(uint32_t* __restrict__ done, co
   const uint32_t nl = sm[16];
   for (uint32_t k = 0; k < nl; ++k) {
     const int u = (int)list[k];
-    body_paint_halo(halo, g, rho, nb, u);
+    sum_faces(u);
     __syncthreads();
     if (threadIdx.x == 0) done[u] = 0u;
   }
+}
+
+__device__ __forceinline__ void paint_faces_last(uint32_t* __restrict__ done, const unsigned long long* halo,
+                                                 const Geom& g, float* __restrict__ rho, int tile, uint32_t* sm) {
+  faces_last(done, halo, g, tile, sm, [&](int u) { body_paint_halo(halo, g, rho, sm, u); });
 }
 
 // ---------------------------------------------------------------- readout (+ kick, drift)
