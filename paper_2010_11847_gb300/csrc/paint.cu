@@ -423,39 +423,64 @@ template <bool F4>
 __global__ void __launch_bounds__(256) k_gather_adj(const float* __restrict__ dx, Geom g, size_t N, size_t M,
                                                     const float* __restrict__ g_rho, const float* __restrict__ F,
                                                     const float* __restrict__ v, float* __restrict__ g_dx,
-                                                    int accumulate) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+                                                    int accumulate, int iters) {
+  // each block walks a contiguous chunk of iters*256 particles (the mesh
+  // rows its lattice rows share stay in L1) and fetches the next particle's
+  // dx and v while it gathers; per-particle arrays are streamed so that L2
+  // keeps the meshes
   const int nc = g.nc;
-  int q[3], c[3];
-  float t[3];
-  lattice_node((uint32_t)i, g, q);
-  for (int a = 0; a < 3; ++a) cic_cell(dx[a * N + i], q[a], nc, &c[a], &t[a]);
-  const int c1[3] = {c[0] + 1 == nc ? 0 : c[0] + 1, c[1] + 1 == nc ? 0 : c[1] + 1, c[2] + 1 == nc ? 0 : c[2] + 1};
-  float vi[3] = {0.f, 0.f, 0.f};
-  if (v)
-    for (int a = 0; a < 3; ++a) vi[a] = v[a * N + i];
-  float gsum[3] = {0.f, 0.f, 0.f};
+  const size_t c0 = (size_t)blockIdx.x * iters * blockDim.x;
+  float dn[3] = {0.f, 0.f, 0.f}, vn[3] = {0.f, 0.f, 0.f};
+  {
+    const size_t i = c0 + threadIdx.x;
+    if (i < N)
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
-    const size_t idx = ((size_t)(bx ? c1[0] : c[0]) * nc + (by ? c1[1] : c[1])) * nc + (bz ? c1[2] : c[2]);
-    float s = 0.f;
-    if (g_rho) s = g.mass * __ldg(g_rho + idx);
-    if (v) {
-      if (F4) {
-        const float4 f = __ldg(reinterpret_cast<const float4*>(F) + idx);
-        s = fmaf(vi[0], f.x, fmaf(vi[1], f.y, fmaf(vi[2], f.z, s)));
-      } else {
-        for (int a = 0; a < 3; ++a) s = fmaf(vi[a], __ldg(F + a * M + idx), s);
+      for (int a = 0; a < 3; ++a) {
+        dn[a] = __ldcs(dx + a * N + i);
+        if (v) vn[a] = __ldcs(v + a * N + i);
       }
-    }
-    const float wx = bx ? t[0] : 1.f - t[0], wy = by ? t[1] : 1.f - t[1], wz = bz ? t[2] : 1.f - t[2];
-    gsum[0] = fmaf((bx ? 1.f : -1.f) * wy * wz, s, gsum[0]);
-    gsum[1] = fmaf((by ? 1.f : -1.f) * wx * wz, s, gsum[1]);
-    gsum[2] = fmaf((bz ? 1.f : -1.f) * wx * wy, s, gsum[2]);
   }
-  for (int a = 0; a < 3; ++a) g_dx[a * N + i] = accumulate ? g_dx[a * N + i] + gsum[a] : gsum[a];
+  for (int it = 0; it < iters; ++it) {
+    if (c0 + (size_t)it * blockDim.x >= N) break;
+    const size_t i = c0 + (size_t)it * blockDim.x + threadIdx.x;
+    const float d[3] = {dn[0], dn[1], dn[2]}, vi[3] = {vn[0], vn[1], vn[2]};
+    const size_t inext = i + blockDim.x;
+    if (it + 1 < iters && inext < N)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dn[a] = __ldcs(dx + a * N + inext);
+        if (v) vn[a] = __ldcs(v + a * N + inext);
+      }
+    if (i >= N) continue;
+    int q[3], c[3];
+    float t[3];
+    lattice_node((uint32_t)i, g, q);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+    const int c1[3] = {c[0] + 1 == nc ? 0 : c[0] + 1, c[1] + 1 == nc ? 0 : c[1] + 1, c[2] + 1 == nc ? 0 : c[2] + 1};
+    float gsum[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
+      const size_t idx = ((size_t)(bx ? c1[0] : c[0]) * nc + (by ? c1[1] : c[1])) * nc + (bz ? c1[2] : c[2]);
+      float s = 0.f;
+      if (g_rho) s = g.mass * __ldg(g_rho + idx);
+      if (v) {
+        if (F4) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(F) + idx);
+          s = fmaf(vi[0], f.x, fmaf(vi[1], f.y, fmaf(vi[2], f.z, s)));
+        } else {
+          for (int a = 0; a < 3; ++a) s = fmaf(vi[a], __ldg(F + a * M + idx), s);
+        }
+      }
+      const float wx = bx ? t[0] : 1.f - t[0], wy = by ? t[1] : 1.f - t[1], wz = bz ? t[2] : 1.f - t[2];
+      gsum[0] = fmaf((bx ? 1.f : -1.f) * wy * wz, s, gsum[0]);
+      gsum[1] = fmaf((by ? 1.f : -1.f) * wx * wz, s, gsum[1]);
+      gsum[2] = fmaf((bz ? 1.f : -1.f) * wx * wy, s, gsum[2]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) __stcs(g_dx + a * N + i, accumulate ? __ldcs(g_dx + a * N + i) + gsum[a] : gsum[a]);
+  }
 }
 
 // max |v| over n values as the bit pattern of a non-negative float (the
@@ -614,10 +639,12 @@ __global__ void __launch_bounds__(768) k_halo_vec(const unsigned long long* __re
 
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
                       const float* v, float* g_dx, bool accumulate, cudaStream_t s) {
+  const int it = readout_iters(c.N);
   if (f4)
-    k_gather_adj<true><<<grid_of(c.N, 256), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate);
+    k_gather_adj<true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate, it);
   else
-    k_gather_adj<false><<<grid_of(c.N, 256), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate);
+    k_gather_adj<false><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate,
+                                                               it);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
