@@ -160,9 +160,14 @@ int fpm_readout(fpm_plan* plan, const float* F, const float* dx, float* f_out,
  * closing kick of a step and the opening kick of the next are applied as
  * one.  The coefficients are computed on the GPU in FP64.  ckpt (NULL to
  * skip): float[nsteps+1][3][np^3], receives dx at every a_k (the momenta
- * are not needed to reverse the steps: the force depends on dx only). */
+ * are not needed to reverse the steps: the force depends on dx only).
+ * fckpt (NULL to skip): float[nsteps+1][4 nc^3], receives the force mesh of
+ * every a_k in the plan's internal layout (float4 per cell on power-of-two
+ * meshes, else [3][nc^3]); fpm_kdk_adj then reuses it instead of
+ * recomputing the forces (the forces are computed straight into it: no
+ * extra traffic, 4 nc^3 floats of memory per stage). */
 int fpm_kdk(fpm_plan* plan, float* dx, float* p, const double* a, int nsteps,
-            float* ckpt, void* stream);
+            float* ckpt, float* fckpt, void* stream);
 
 /* Binned power spectrum (Eq. 10's ingredient) of mesh field `a`, or the
  * cross spectrum of `a` and `b` (b may be NULL):
@@ -223,15 +228,17 @@ int fpm_readout_adj(fpm_plan* plan, const float* F, const float* dx, const float
 int fpm_force_adj(fpm_plan* plan, const float* g_F, float* g_rho, void* stream);
 
 /* Reverse of fpm_kdk over the same HOST scale factors a[0..nsteps], given
- * its checkpoints ckpt (float[nsteps+1][3][np^3], dx at every a_k).  On
- * entry g_dx holds the cotangent of the final dx and g_p_in (nullable:
- * zero, e.g. a loss on the density alone) that of the final p; on return
- * g_dx and g_p (required, may equal g_p_in) hold the cotangents of the
- * initial dx and p.  Each reverse step recomputes the force at the
- * checkpoint, then applies the drift transpose and the transposed force
- * Jacobian (readout, force and paint transposes). */
-int fpm_kdk_adj(fpm_plan* plan, const float* ckpt, const double* a, int nsteps, float* g_dx,
-                const float* g_p_in, float* g_p, void* stream);
+ * its checkpoints ckpt (float[nsteps+1][3][np^3], dx at every a_k) and,
+ * optionally, its force checkpoints fckpt (NULL: recompute).  On entry g_dx
+ * holds the cotangent of the final dx and g_p_in (nullable: zero, e.g. a
+ * loss on the density alone) that of the final p; on return g_dx and g_p
+ * (required, may equal g_p_in) hold the cotangents of the initial dx and p.
+ * Each reverse step buckets the checkpoint's particles by tile and takes its
+ * force from fckpt (or recomputes paint and force), then applies the drift
+ * transpose and the transposed force Jacobian (readout, force and paint
+ * transposes).  The result is bitwise the same either way. */
+int fpm_kdk_adj(fpm_plan* plan, const float* ckpt, const float* fckpt, const double* a, int nsteps,
+                float* g_dx, const float* g_p_in, float* g_p, void* stream);
 
 /* Reverse of fpm_lpt: from the cotangents of dx and p (float[3][np^3])
  * returns g_lin_k = DFT(dL/d delta_L), the unnormalised DFT of the

@@ -17,6 +17,20 @@ import torch
 from .binding import Plan
 
 
+# Force checkpoints (the forward's force mesh at every stage) spare the
+# reverse pass a paint and a force per step; they are kept when they fit in
+# the free device memory with this margin to spare.
+FORCE_CKPT_MARGIN_BYTES = 8 << 30
+
+
+def _force_checkpoints(plan: Plan, nstages: int, device):
+    need = nstages * plan.force_ckpt_floats * 4
+    free, _ = torch.cuda.mem_get_info(device)
+    if need + FORCE_CKPT_MARGIN_BYTES > free:
+        return None
+    return torch.empty(nstages, plan.force_ckpt_floats, device=device)
+
+
 class _Chi2OfFinalDensity(torch.autograd.Function):
     @staticmethod
     def forward(ctx, white, target, plan: Plan, a, sigma: float, order: int):
@@ -24,19 +38,21 @@ class _Chi2OfFinalDensity(torch.autograd.Function):
         lin_k = plan.linear_field(white.contiguous())
         dx, p = plan.lpt(lin_k, float(a[0]), order)
         ckpt = torch.empty(len(a), 3, plan.N, device=white.device)
-        plan.kdk(dx, p, a, ckpt=ckpt)
+        fckpt = _force_checkpoints(plan, len(a), white.device)
+        plan.kdk(dx, p, a, ckpt=ckpt, fckpt=fckpt)
         rho = plan.paint(dx)
         loss, g_rho = plan.chi2(rho, target.contiguous(), sigma)
         ctx.plan, ctx.a, ctx.order = plan, a, order
-        ctx.save_for_backward(lin_k, ckpt, g_rho)
+        ctx.has_fckpt = fckpt is not None
+        ctx.save_for_backward(lin_k, ckpt, g_rho, fckpt if fckpt is not None else ckpt[:0])
         return torch.tensor(loss, dtype=torch.float64, device=white.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        lin_k, ckpt, g_rho = ctx.saved_tensors
+        lin_k, ckpt, g_rho, fckpt = ctx.saved_tensors
         plan, a = ctx.plan, ctx.a
         g_dx = plan.paint_adj(ckpt[-1], g_rho)
-        g_dx, g_p = plan.kdk_adj(ckpt, a, g_dx)
+        g_dx, g_p = plan.kdk_adj(ckpt, a, g_dx, fckpt=fckpt if ctx.has_fckpt else None)
         g_lin_k = plan.lpt_adj(lin_k, float(a[0]), g_dx, g_p, ctx.order)
         g_white = plan.linear_field_adj(g_lin_k)
         return g_white * grad_out.to(g_white.dtype), None, None, None, None, None

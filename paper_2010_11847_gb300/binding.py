@@ -64,7 +64,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_paint.argtypes = [vp, vp, vp, vp, vp, vp]
     L.fpm_force.argtypes = [vp, vp, vp, vp]
     L.fpm_readout.argtypes = [vp, vp, vp, vp, vp]
-    L.fpm_kdk.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.fpm_kdk.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
     L.fpm_power.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_status.argtypes = [vp, vp]
     L.fpm_strerror.argtypes = [i]
@@ -83,7 +83,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_paint_adj.argtypes = [vp, vp, vp, vp, vp]
     L.fpm_readout_adj.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_force_adj.argtypes = [vp, vp, vp, vp]
-    L.fpm_kdk_adj.argtypes = [vp, vp, vp, i, vp, vp, vp, vp]
+    L.fpm_kdk_adj.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp]
     L.fpm_lpt_adj.argtypes = [vp, vp, d, i, vp, vp, vp, vp]
     L.fpm_linear_field_adj.argtypes = [vp, vp, vp, vp]
     L.fpm_batch_create.argtypes = [ctypes.POINTER(vp), vp, i]
@@ -217,11 +217,18 @@ class Plan:
         _check("fpm_readout", lib().fpm_readout(self._h, _ptr(F), _ptr(dx), _ptr(f_out), _stream(stream)))
         return f_out
 
-    def kdk(self, dx, p, a, ckpt=None, stream=None):
+    def kdk(self, dx, p, a, ckpt=None, fckpt=None, stream=None):
+        """KDK steps over the scale factors a; ckpt [len(a), 3, N] receives dx
+        at every stage, fckpt [len(a), force_ckpt_floats] the force meshes."""
         a = _host_f64(a).ravel()
         _check("fpm_kdk", lib().fpm_kdk(self._h, _ptr(dx), _ptr(p), a.ctypes.data, a.size - 1, _ptr(ckpt),
-                                        _stream(stream)))
+                                        _ptr(fckpt), _stream(stream)))
         return dx, p
+
+    @property
+    def force_ckpt_floats(self) -> int:
+        """Floats per stage of a force checkpoint (4 nc^3)."""
+        return 4 * self.M
 
     def power(self, a, b=None, stream=None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
         nb = self.nc // 2
@@ -283,13 +290,14 @@ class Plan:
         _check("fpm_force_adj", lib().fpm_force_adj(self._h, _ptr(g_F), _ptr(g_rho), _stream(stream)))
         return g_rho
 
-    def kdk_adj(self, ckpt, a, g_dx, g_p_in=None, g_p=None, stream=None):
+    def kdk_adj(self, ckpt, a, g_dx, g_p_in=None, g_p=None, fckpt=None, stream=None):
         """Cotangents of the initial (dx, p) from those of the final ones
-        (g_p_in None: the loss does not depend on the final momenta)."""
+        (g_p_in None: the loss does not depend on the final momenta); fckpt:
+        the forward's force checkpoints (None: recompute the forces)."""
         a = _host_f64(a).ravel()
         g_p = g_p if g_p is not None else self._empty(3, self.N)
-        _check("fpm_kdk_adj", lib().fpm_kdk_adj(self._h, _ptr(ckpt), a.ctypes.data, a.size - 1, _ptr(g_dx),
-                                                _ptr(g_p_in), _ptr(g_p), _stream(stream)))
+        _check("fpm_kdk_adj", lib().fpm_kdk_adj(self._h, _ptr(ckpt), _ptr(fckpt), a.ctypes.data, a.size - 1,
+                                                _ptr(g_dx), _ptr(g_p_in), _ptr(g_p), _stream(stream)))
         return g_dx, g_p
 
     def lpt_adj(self, lin_k, a0, g_dx, g_p, order=2, g_lin_k=None, stream=None):

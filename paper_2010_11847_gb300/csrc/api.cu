@@ -440,7 +440,8 @@ int fpm_readout(fpm_plan* p, const float* F, const float* dx, float* f_out, void
   return timed(p, FPM_K_READOUT, 1, s, [&] { return launch_readout(p->pc, F, dx, f_out, s); });
 }
 
-int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, float* ckpt, void* stream) {
+int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, float* ckpt, float* fckpt,
+            void* stream) {
   if (!p || !dx || !mom || !a || nsteps < 0 || nsteps > MAX_STEPS) return FPM_EINVAL;
   if (nsteps == 0) return FPM_OK;
   for (int k = 0; k <= nsteps; ++k)
@@ -453,23 +454,26 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
     return launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s);
   }));
   const size_t N = p->N;
+  // the force of stage k is computed straight into its checkpoint slot when
+  // the caller keeps them (the reverse pass then reuses it)
+  auto Fk = [&](int k) { return fckpt ? fckpt + (size_t)k * 4 * p->M : p->F; };
   if (ckpt) FPM_CUDA_TRY(cudaMemcpyAsync(ckpt, dx, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   FPM_TRY(paint_impl(p, dx, p->rho, nullptr, nullptr, s));
-  FPM_TRY(force_impl(p, p->rho, p->F, s, p->f4));
+  FPM_TRY(force_impl(p, p->rho, Fk(0), s, p->f4));
   for (int k = 0; k < nsteps; ++k) {
     // closing kick of step k-1 and opening kick of step k share the force at a_k
     const int ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
     FPM_TRY(timed(p, FPM_K_KDK, 1, s, [&] {
-      return launch_kdk(p->pc, dx, mom, p->F, p->f4, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
+      return launch_kdk(p->pc, dx, mom, Fk(k), p->f4, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
     }));
     if (ckpt)
       FPM_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(k + 1) * 3 * N, dx, 3 * N * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s));
     FPM_TRY(sort_paint_impl(p, p->pc, dx, p->rho, nullptr, s));
-    FPM_TRY(force_impl(p, p->rho, p->F, s, p->f4));
+    FPM_TRY(force_impl(p, p->rho, Fk(k + 1), s, p->f4));
   }
   return timed(p, FPM_K_KDK, 1, s, [&] {
-    return launch_kdk(p->pc, dx, mom, p->F, p->f4, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
+    return launch_kdk(p->pc, dx, mom, Fk(nsteps), p->f4, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
   });
 }
 
@@ -643,12 +647,20 @@ static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream
 
 // gx += J_f(x)^T v at the positions x whose paint (buckets) and force
 // meshes (p->F, interleaved when p->f4) are current; uses p->rho as scratch.
-static int force_jt_impl(fpm_plan* p, const float* x, const float* v, float* gx, cudaStream_t s) {
+static int force_jt_impl(fpm_plan* p, const float* x, const float* v, float* gx, const float* F, cudaStream_t s) {
   FPM_TRY(timed(p, FPM_K_PAINT, p->pc.tile_done ? 4 : 7, s,
                 [&] { return launch_paint_vec(p->pc, x, v, p->vmax, p->gF, s); }));
   FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
   return timed(p, FPM_K_READOUT, 1, s,
-               [&] { return launch_gather_adj(p->pc, x, p->rho, p->F, p->f4, v, gx, true, s); });
+               [&] { return launch_gather_adj(p->pc, x, p->rho, F, p->f4, v, gx, true, s); });
+}
+
+// Tile buckets (and in-tile cells) of positions x, without the paint.
+static int sort_impl(fpm_plan* p, const float* x, cudaStream_t s) {
+  PaintCtx c = p->pc;
+  FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, x, s); }));
+  FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
+  return timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); });
 }
 
 extern "C" {
@@ -714,8 +726,8 @@ int fpm_force_adj(fpm_plan* p, const float* g_F, float* g_rho, void* stream) {
   return force_adj_impl(p, g_F, g_rho, S(stream));
 }
 
-int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const double* a, int nsteps, float* g_dx, const float* g_p_in,
-                float* g_p, void* stream) {
+int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const float* fckpt, const double* a, int nsteps, float* g_dx,
+                const float* g_p_in, float* g_p, void* stream) {
   if (!p || !ckpt || !a || !g_dx || !g_p || nsteps < 1 || nsteps > MAX_STEPS) return FPM_EINVAL;
   for (int k = 0; k <= nsteps; ++k)
     if (!(a[k] > 1e-5 && a[k] <= 10.0) || (k > 0 && !(a[k] > a[k - 1]))) return FPM_EINVAL;
@@ -735,15 +747,23 @@ int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const double* a, int nsteps, flo
   } else {     // the loss does not depend on the final momenta: start from zero
     FPM_CUDA_TRY(cudaMemsetAsync(gp, 0, N3 * sizeof(float), s));
   }
-  auto recompute = [&](const float* x) -> int {
+  // the force at stage k and the tile buckets of x_k: from the forward's
+  // force checkpoint (buckets only), or recomputed (paint + force)
+  const float* Fk = p->F;
+  auto prepare = [&](int k, const float* x) -> int {
+    if (fckpt) {
+      Fk = fckpt + (size_t)k * 4 * p->M;
+      return sort_impl(p, x, s);
+    }
+    Fk = p->F;
     FPM_TRY(paint_impl(p, x, p->rho, nullptr, nullptr, s));
     return force_impl(p, p->rho, p->F, s, p->f4);
   };
   if (g_p_in) {   // closing half kick at a_n: gx += J^T(x_n) (K gp)
     const float* xn = ckpt + (size_t)nsteps * N3;
-    FPM_TRY(recompute(xn));
+    FPM_TRY(prepare(nsteps, xn));
     FPM_TRY(launch_scale_copy(gp, p->vbuf, N3, p->d_fac, 3 * (nsteps - 1) + 2, s));
-    FPM_TRY(force_jt_impl(p, xn, p->vbuf, g_dx, s));
+    FPM_TRY(force_jt_impl(p, xn, p->vbuf, g_dx, Fk, s));
   }
   for (int k = nsteps - 1; k >= 0; --k) {
     const float* xk = ckpt + (size_t)k * N3;
@@ -751,8 +771,8 @@ int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const double* a, int nsteps, flo
     // and closing kick of step k-1 share the force at a_k)
     FPM_TRY(launch_adj_drift_kick(g_dx, gp, p->vbuf, N3, p->d_fac, 3 * k + 1, 3 * k + 0,
                                   k > 0 ? 3 * (k - 1) + 2 : -1, s));
-    FPM_TRY(recompute(xk));
-    FPM_TRY(force_jt_impl(p, xk, p->vbuf, g_dx, s));
+    FPM_TRY(prepare(k, xk));
+    FPM_TRY(force_jt_impl(p, xk, p->vbuf, g_dx, Fk, s));
   }
   g_launches += 1 + 2 * nsteps;
   return FPM_OK;

@@ -57,7 +57,7 @@ def test_plan_rejects_bad_cosmology(libfpm):
 def test_null_plan_entry_points(libfpm):
     assert libfpm.fpm_paint(None, None, None, None, None, None) == binding.FPM_EINVAL
     assert libfpm.fpm_force(None, None, None, None) == binding.FPM_EINVAL
-    assert libfpm.fpm_kdk(None, None, None, None, 1, None, None) == binding.FPM_EINVAL
+    assert libfpm.fpm_kdk(None, None, None, None, 1, None, None, None) == binding.FPM_EINVAL
     assert libfpm.fpm_status(None, None) == binding.FPM_EINVAL
     libfpm.fpm_plan_destroy(None)
 

@@ -180,3 +180,32 @@ def test_differentiable_config_gradient(torch_mod):
         print(f"FP32 directional derivative eps={eps:g}: rel error "
               f"{abs(dds[eps] - float(ad @ u[idx])) / abs(float(ad @ u[idx])):.2e}")
     assert abs(dds[3e-2] - float(ad @ u[idx])) < 3e-2 * abs(float(ad @ u[idx]))
+
+
+@pytest.mark.parametrize("np_,nc,reverse", [(32, 64, True), (32, 32, True), (48, 96, False)])
+def test_force_checkpoints_give_the_same_bits(torch_mod, np_, nc, reverse):
+    """Keeping the forward's force meshes (fckpt) changes nothing but the
+    work: the same forward state and checkpoints (float4 and planar force
+    meshes), and the same cotangents as the reverse pass that recomputes the
+    forces (the reverse pass runs on power-of-two meshes)."""
+    torch = torch_mod
+    stages = np.linspace(0.1, 0.7, 4)
+    pl = plan(np_, nc)
+    lk = pl.linear_field(dev(inputs.white_noise(np_, 9), torch))
+    dx, p = pl.lpt(lk, float(stages[0]), 2)
+    dx2, p2 = dx.clone(), p.clone()
+    ck = torch.empty(len(stages), 3, pl.N, device="cuda")
+    ck2 = torch.empty_like(ck)
+    fck = torch.empty(len(stages), pl.force_ckpt_floats, device="cuda")
+    pl.kdk(dx, p, stages, ckpt=ck)
+    pl.kdk(dx2, p2, stages, ckpt=ck2, fckpt=fck)
+    assert torch.equal(dx, dx2) and torch.equal(p, p2) and torch.equal(ck, ck2)
+    if not reverse:
+        return
+    gdx = dev(inputs.random_displacements(np_, 1.0, 6), torch)
+    gp = dev(inputs.random_displacements(np_, 1.0, 7), torch)
+    r1 = pl.kdk_adj(ck, stages, gdx.clone(), g_p_in=gp.clone())
+    r2 = pl.kdk_adj(ck, stages, gdx.clone(), g_p_in=gp.clone(), fckpt=fck)
+    torch.cuda.synchronize()
+    assert pl.status() == 0
+    assert torch.equal(r1[0], r2[0]) and torch.equal(r1[1], r2[1])
