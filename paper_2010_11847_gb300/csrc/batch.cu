@@ -41,6 +41,7 @@ struct SimDesc {
   float2* spec;
   size_t specmax;
   uint32_t *keys, *items, *tile_count, *tile_start, *tile_cursor;
+  uint16_t* cells;               // in-tile cell of each item (written by the scatter phase)
   unsigned long long* halo;
   int* err;
   const double* fac;
@@ -184,9 +185,11 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
           break;
         }
         case PH_SCAN: body_scan_tiles(d.tile_count, d.ntiles, d.tile_start, d.tile_cursor, su, 1); break;
-        case PH_SCATTER: body_scatter(d.keys, d.N, d.tile_cursor, d.items, local); break;
-        case PH_PAINT: body_paint_bucket<true>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err, su,
-                                         su + ACC, local); break;
+        case PH_SCATTER: body_scatter_cube(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su); break;
+        case PH_PAINT:
+          body_paint_bucket_acc<true>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err,
+                                      Acc32{su, su + ACC}, local, d.cells);
+          break;
         case PH_HALO: body_paint_halo(d.halo, d.g, d.rho, su, local); break;
         default:
           switch (d.nc) {
@@ -211,7 +214,7 @@ static void items_for(SimDesc& d, int ro_iters) {
   d.items_of[PH_KDK] = (int)((d.N + pchunk - 1) / pchunk);
   d.items_of[PH_KDK_LAST] = d.items_of[PH_KDK];
   d.items_of[PH_SCAN] = 1;
-  d.items_of[PH_SCATTER] = (int)((d.N + (size_t)BT * SCAT_E - 1) / ((size_t)BT * SCAT_E));
+  d.items_of[PH_SCATTER] = scatter_cube_items(d.g.np, BT);
   d.items_of[PH_PAINT] = d.ntiles;
   d.items_of[PH_HALO] = d.ntiles;
   int L = 0;
@@ -330,6 +333,7 @@ int batch_create(Batch** out, const BatchPlanView* views, int nsims) {
     d.specmax = v.specmax;
     d.keys = v.pc.keys;
     d.items = v.pc.items;
+    d.cells = v.pc.cells;
     d.tile_count = v.pc.tile_count;
     d.tile_start = v.pc.tile_start;
     d.tile_cursor = v.pc.tile_cursor;

@@ -40,97 +40,20 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(uint32_t* __restric
   body_scan_tiles(count, ntiles, start, cursor, part, 0);
 }
 
-__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ keys, size_t N,
-                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ items) {
-  body_scatter(keys, N, cursor, items, blockIdx.x);
-}
 
-// Bucketing by tile, aggregated per Lagrangian cube: block (cx, cy, cz)
-// takes the 16^3 particles of one lattice cube (8 per thread), whose cells
-// fall in few tiles.  Each warp groups its 32 keys by tile (match_any); the
-// group leader registers the tile in a shared open-addressing table and
-// reserves the group's places in that tile's shared count; then one global
-// cursor atomic per (cube, tile) reserves the cube's range of the bucket.
-// A tile that finds the table full takes its places with a global atomic
-// per warp group instead.  Order inside a bucket is not fixed (the paint's
-// integer sums and the stable sort of the permutation output do not depend
-// on it).
 constexpr int SC_THREADS = 512;
 // The cube bucketing also records each item's in-tile cell for the paints.
 constexpr bool PAINT_CELLS = true;
-constexpr int SC_CUBE = 16;
-constexpr int SC_PER = SC_CUBE * SC_CUBE * SC_CUBE / SC_THREADS;   // 8
-constexpr int SC_TBL = 256;
 
-// In-tile cells recorded by the cube bucketing (null where it did not run).
-inline uint16_t* cells_of(const PaintCtx& c) {
-  return (PAINT_CELLS && c.g.np % SC_CUBE == 0) ? c.cells : nullptr;
-}
-
-__device__ __forceinline__ uint32_t cube_index(int e, int t, int cx, int cy, int cz, int np) {
-  const int l = e * SC_THREADS + t;
-  const int lx = l >> 8, ly = (l >> 4) & 15, lz = l & 15;
-  return ((uint32_t)(cx * SC_CUBE + lx) * np + (uint32_t)(cy * SC_CUBE + ly)) * np + (uint32_t)(cz * SC_CUBE + lz);
-}
+// In-tile cells recorded by the cube bucketing.
+inline uint16_t* cells_of(const PaintCtx& c) { return PAINT_CELLS ? c.cells : nullptr; }
 
 __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                              uint32_t* __restrict__ cursor,
                                                              uint32_t* __restrict__ items,
                                                              uint16_t* __restrict__ cells) {
-  __shared__ uint32_t t_tile[SC_TBL], t_cnt[SC_TBL], t_base[SC_TBL];
-  const unsigned full = 0xffffffffu;
-  const int t = threadIdx.x, lane = t & 31;
-  const int ncube = np / SC_CUBE;
-  const int cz = blockIdx.x % ncube, cy = (blockIdx.x / ncube) % ncube, cx = blockIdx.x / (ncube * ncube);
-  uint32_t key[SC_PER];
-#pragma unroll
-  for (int e = 0; e < SC_PER; ++e) key[e] = __ldcg(keys + cube_index(e, t, cx, cy, cz, np));
-  for (int k = t; k < SC_TBL; k += SC_THREADS) {
-    t_tile[k] = 0xffffffffu;
-    t_cnt[k] = 0;
-  }
-  __syncthreads();
-  uint32_t packed[SC_PER];   // slot << 16 | place in the cube's range; ~0 once written directly
-#pragma unroll
-  for (int e = 0; e < SC_PER; ++e) {
-    const uint32_t tile = key[e] >> 12;
-    const unsigned grp = __match_any_sync(full, tile);
-    const int leader = __ffs(grp) - 1;
-    int sl = -1;
-    uint32_t off = 0;
-    if (lane == leader) {
-      uint32_t h = (tile * 2654435761u) >> 24;
-      for (int probe = 0; probe < SC_TBL; ++probe, h = (h + 1) & (SC_TBL - 1)) {
-        const uint32_t prev = atomicCAS(&t_tile[h], 0xffffffffu, tile);
-        if (prev == 0xffffffffu || prev == tile) {
-          sl = (int)h;
-          break;
-        }
-      }
-      off = sl >= 0 ? atomicAdd(&t_cnt[sl], (uint32_t)__popc(grp))
-                    : atomicAdd(cursor + tile, (uint32_t)__popc(grp));   // table full: direct
-    }
-    sl = __shfl_sync(full, sl, leader);
-    const uint32_t place = __shfl_sync(full, off, leader) + __popc(grp & ((1u << lane) - 1u));
-    if (sl < 0) {
-      items[place] = cube_index(e, t, cx, cy, cz, np);
-      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
-      packed[e] = 0xffffffffu;
-    } else {
-      packed[e] = ((uint32_t)sl << 16) | place;
-    }
-  }
-  __syncthreads();
-  for (int k = t; k < SC_TBL; k += SC_THREADS)
-    if (t_tile[k] != 0xffffffffu) t_base[k] = atomicAdd(cursor + t_tile[k], t_cnt[k]);
-  __syncthreads();
-#pragma unroll
-  for (int e = 0; e < SC_PER; ++e)
-    if (packed[e] != 0xffffffffu) {
-      const uint32_t place = t_base[packed[e] >> 16] + (packed[e] & 0xffffu);
-      items[place] = cube_index(e, t, cx, cy, cz, np);
-      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
-    }
+  __shared__ uint32_t tbl[3 * SC_TBL];
+  body_scatter_cube(keys, np, cursor, items, cells, blockIdx.x, tbl);
 }
 
 __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,
@@ -351,12 +274,9 @@ int launch_scan(const PaintCtx& c, cudaStream_t s) {
 }
 
 int launch_scatter(const PaintCtx& c, cudaStream_t s) {
-  if (c.g.np % SC_CUBE == 0) {
-    const int nq = c.g.np / SC_CUBE;
-    k_scatter_cube<<<nq * nq * nq, SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor, c.items, cells_of(c));
-  } else {
-    k_scatter<<<grid_of(c.N, 256 * SCAT_E), 256, 0, s>>>(c.keys, c.N, c.tile_cursor, c.items);
-  }
+  if (c.g.np % SC_CUBE != 0) return FPM_EINVAL;   // every supported lattice size is a multiple of 16
+  k_scatter_cube<<<scatter_cube_items(c.g.np, SC_THREADS), SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor,
+                                                                             c.items, cells_of(c));
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }

@@ -155,33 +155,92 @@ __device__ __forceinline__ void body_scan_tiles(uint32_t* __restrict__ count, in
 }
 
 // ---------------------------------------------------------------- bucket by tile
-// Each thread places SCAT_E particles; the cursor atomics of its chunks are
-// issued back to back so their round trips to L2 overlap.
-constexpr int SCAT_E = 4;
-__device__ __forceinline__ void body_scatter(const uint32_t* __restrict__ keys, size_t N, uint32_t* __restrict__ cursor,
-                                             uint32_t* __restrict__ items, int bx) {
+// Bucketing by tile, aggregated per Lagrangian cube: work item `item` takes
+// the 16 x 16 x CX particles of one lattice block (CX = 8 blockDim / 256: 8
+// per thread), whose cells fall in few tiles.  Each warp groups its 32 keys
+// by tile (match_any); the group leader registers the tile in a shared
+// open-addressing table and reserves the group's places in that tile's
+// shared count; then one global cursor atomic per (block, tile) reserves the
+// block's range of the bucket.  A tile that finds the table full takes its
+// places with a global atomic per warp group instead.  Beside each item the
+// in-tile cell (the key's low 12 bits) goes to cells (if not null).  Order
+// inside a bucket is not fixed: the paint's integer sums and the stable sort
+// of the permutation output do not depend on it.  tbl: 3 SC_TBL words of
+// shared memory.  np must be a multiple of 16.
+constexpr int SC_CUBE = 16;
+constexpr int SC_PER = 8;
+constexpr int SC_TBL = 256;
+
+__host__ __device__ inline int scatter_cube_items(int np, int threads) {
+  const int cx = SC_PER * threads / (SC_CUBE * SC_CUBE);
+  return (np / cx) * (np / SC_CUBE) * (np / SC_CUBE);
+}
+
+__device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ keys, int np,
+                                                  uint32_t* __restrict__ cursor, uint32_t* __restrict__ items,
+                                                  uint16_t* __restrict__ cells, int item, uint32_t* tbl) {
+  uint32_t* t_tile = tbl;
+  uint32_t* t_cnt = tbl + SC_TBL;
+  uint32_t* t_base = tbl + 2 * SC_TBL;
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const size_t i0 = (size_t)bx * blockDim.x * SCAT_E + threadIdx.x;
-  int tile[SCAT_E];
-  unsigned grp[SCAT_E];
-  uint32_t base[SCAT_E];
+  const int t = threadIdx.x, lane = t & 31, nt = blockDim.x;
+  const int cxw = SC_PER * nt / (SC_CUBE * SC_CUBE);          // x extent of the block of particles
+  const int nq = np / SC_CUBE;
+  const int cz = item % nq, cy = (item / nq) % nq, cx = item / (nq * nq);
+  auto index_of = [&](int e) -> uint32_t {
+    const int l = e * nt + t;
+    const int lx = l >> 8, ly = (l >> 4) & 15, lz = l & 15;
+    return ((uint32_t)(cx * cxw + lx) * np + (uint32_t)(cy * SC_CUBE + ly)) * np + (uint32_t)(cz * SC_CUBE + lz);
+  };
+  uint32_t key[SC_PER];
 #pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    const size_t i = i0 + (size_t)e * blockDim.x;
-    tile[e] = i < N ? (int)(__ldcg(keys + i) >> 12) : -1 - lane;
-    grp[e] = __match_any_sync(full, tile[e]);
+  for (int e = 0; e < SC_PER; ++e) key[e] = __ldcg(keys + index_of(e));
+  for (int k = t; k < SC_TBL; k += nt) {
+    t_tile[k] = 0xffffffffu;
+    t_cnt[k] = 0;
   }
+  __syncthreads();
+  uint32_t packed[SC_PER];   // slot << 16 | place in the block's range; ~0 once written directly
 #pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    base[e] = 0;
-    if (tile[e] >= 0 && lane == __ffs(grp[e]) - 1) base[e] = atomicAdd(cursor + tile[e], (uint32_t)__popc(grp[e]));
+  for (int e = 0; e < SC_PER; ++e) {
+    const uint32_t tile = key[e] >> 12;
+    const unsigned grp = __match_any_sync(full, tile);
+    const int leader = __ffs(grp) - 1;
+    int sl = -1;
+    uint32_t off = 0;
+    if (lane == leader) {
+      uint32_t h = (tile * 2654435761u) >> 24;
+      for (int probe = 0; probe < SC_TBL; ++probe, h = (h + 1) & (SC_TBL - 1)) {
+        const uint32_t prev = atomicCAS(&t_tile[h], 0xffffffffu, tile);
+        if (prev == 0xffffffffu || prev == tile) {
+          sl = (int)h;
+          break;
+        }
+      }
+      off = sl >= 0 ? atomicAdd(&t_cnt[sl], (uint32_t)__popc(grp))
+                    : atomicAdd(cursor + tile, (uint32_t)__popc(grp));   // table full: direct
+    }
+    sl = __shfl_sync(full, sl, leader);
+    const uint32_t place = __shfl_sync(full, off, leader) + __popc(grp & ((1u << lane) - 1u));
+    if (sl < 0) {
+      items[place] = index_of(e);
+      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
+      packed[e] = 0xffffffffu;
+    } else {
+      packed[e] = ((uint32_t)sl << 16) | place;
+    }
   }
+  __syncthreads();
+  for (int k = t; k < SC_TBL; k += nt)
+    if (t_tile[k] != 0xffffffffu) t_base[k] = atomicAdd(cursor + t_tile[k], t_cnt[k]);
+  __syncthreads();
 #pragma unroll
-  for (int e = 0; e < SCAT_E; ++e) {
-    const uint32_t b = __shfl_sync(full, base[e], __ffs(grp[e]) - 1);
-    if (tile[e] >= 0) items[b + __popc(grp[e] & ((1u << lane) - 1u))] = (uint32_t)(i0 + (size_t)e * blockDim.x);
-  }
+  for (int e = 0; e < SC_PER; ++e)
+    if (packed[e] != 0xffffffffu) {
+      const uint32_t place = t_base[packed[e] >> 16] + (packed[e] & 0xffffu);
+      items[place] = index_of(e);
+      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
+    }
 }
 
 // ---------------------------------------------------------------- fixed point
