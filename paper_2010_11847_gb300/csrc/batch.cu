@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
           break;
         }
         case PH_SCAN: body_scan_tiles(d.tile_count, d.ntiles, d.tile_start, d.tile_cursor, su, 1); break;
-        case PH_SCATTER: body_scatter_cube(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su); break;
+        case PH_SCATTER: body_scatter_cube<BT>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su); break;
         case PH_PAINT:
           body_paint_bucket_acc<true>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err,
                                       Acc32{su, su + ACC}, local, d.cells);

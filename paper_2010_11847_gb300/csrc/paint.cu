@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* 
                                                              uint32_t* __restrict__ items,
                                                              uint16_t* __restrict__ cells) {
   __shared__ uint32_t tbl[3 * SC_TBL];
-  body_scatter_cube(keys, np, cursor, items, cells, blockIdx.x, tbl);
+  body_scatter_cube<SC_THREADS>(keys, np, cursor, items, cells, blockIdx.x, tbl);
 }
 
 __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,

@@ -156,7 +156,7 @@ __device__ __forceinline__ void body_scan_tiles(uint32_t* __restrict__ count, in
 
 // ---------------------------------------------------------------- bucket by tile
 // Bucketing by tile, aggregated per Lagrangian cube: work item `item` takes
-// the 16 x 16 x CX particles of one lattice block (CX = 8 blockDim / 256: 8
+// the 16 x 16 x CX particles of one lattice block (CX = 8 NT / 256: 8
 // per thread), whose cells fall in few tiles.  Each warp groups its 32 keys
 // by tile (match_any); the group leader registers the tile in a shared
 // open-addressing table and reserves the group's places in that tile's
@@ -165,8 +165,8 @@ __device__ __forceinline__ void body_scan_tiles(uint32_t* __restrict__ count, in
 // places with a global atomic per warp group instead.  Beside each item the
 // in-tile cell (the key's low 12 bits) goes to cells (if not null).  Order
 // inside a bucket is not fixed: the paint's integer sums and the stable sort
-// of the permutation output do not depend on it.  tbl: 3 SC_TBL words of
-// shared memory.  np must be a multiple of 16.
+// of the permutation output do not depend on it.  NT: the block's threads;
+// tbl: 3 SC_TBL words of shared memory.  np must be a multiple of 16.
 constexpr int SC_CUBE = 16;
 constexpr int SC_PER = 8;
 constexpr int SC_TBL = 256;
@@ -176,6 +176,7 @@ __host__ __device__ inline int scatter_cube_items(int np, int threads) {
   return (np / cx) * (np / SC_CUBE) * (np / SC_CUBE);
 }
 
+template <int NT>
 __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                   uint32_t* __restrict__ cursor, uint32_t* __restrict__ items,
                                                   uint16_t* __restrict__ cells, int item, uint32_t* tbl) {
@@ -183,8 +184,8 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
   uint32_t* t_cnt = tbl + SC_TBL;
   uint32_t* t_base = tbl + 2 * SC_TBL;
   const unsigned full = 0xffffffffu;
-  const int t = threadIdx.x, lane = t & 31, nt = blockDim.x;
-  const int cxw = SC_PER * nt / (SC_CUBE * SC_CUBE);          // x extent of the block of particles
+  const int t = threadIdx.x, lane = t & 31;
+  constexpr int nt = NT, cxw = SC_PER * NT / (SC_CUBE * SC_CUBE);   // x extent of the block of particles
   const int nq = np / SC_CUBE;
   const int cz = item % nq, cy = (item / nq) % nq, cx = item / (nq * nq);
   auto index_of = [&](int e) -> uint32_t {
