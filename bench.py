@@ -258,11 +258,16 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 def kernel_source_hash(files):
-    """Hash of the CUDA sources a kernel class is built from."""
+    """Hash of the code (comments and whitespace runs removed) of the CUDA
+    sources a kernel class is built from."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2010_11847_gb300", "csrc")
     for f in sorted(files):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(re.sub(r"\s+", " ", text).strip().encode())
     return h.hexdigest()[:16]
 
 

@@ -8,8 +8,10 @@
 // floor(dx)), exact in float), tile counts are histogrammed with
 // warp-aggregated atomics into an L2-resident table, scanned, and the
 // particles are bucketed by tile (a counting sort on the tile part of the
-// key).  When the caller asks for the permutation, a shared-memory counting
-// sort by local cell plus an index tie-fix completes the stable order.
+// key), one Lagrangian block of particles per thread block, which records
+// each item's in-tile cell beside it.  When the caller asks for the
+// permutation, a shared-memory counting sort by local cell plus an index
+// tie-fix completes the stable order.
 //
 // Paint.  One CTA per tile accumulates the CIC weights of its bucket into a
 // 17^3 shared-memory block (the tile plus its upper halo).  Each weight is
@@ -17,12 +19,13 @@
 // atomics; a thread whose add wraps the 32-bit word (it sees it in the
 // returned old value) adds the carry to a second word, so every cell holds
 // the exact 64-bit sum.  Before adding, a warp that holds long runs of the
-// same cell merges them (segmented shuffle sums).  Integer addition is
-// associative, so the density does not depend on the order of anything: it
-// is deterministic.  The particle mass multiplies the sums at write-out.
-// Cells that only this tile touches are written directly; the shell of the
-// 17^3 block goes to a per-tile halo buffer that a second kernel sums over
-// the (up to 8) tiles covering each face cell.
+// same cell merges them (one redux.sync per corner over each run's lanes).
+// Integer addition is associative, so the density does not depend on the
+// order of anything: it is deterministic.  The particle mass multiplies the
+// sums at write-out.  Cells that only this tile touches are written
+// directly; the shell of the 17^3 block goes to a per-tile halo buffer, and
+// the last of the (up to 8) blocks whose shells cover a tile's lower faces
+// sums them (a separate face-sum kernel where no face counters are kept).
 #pragma once
 #include "internal.h"
 
