@@ -59,6 +59,11 @@ def test_null_plan_entry_points(libfpm):
     assert libfpm.fpm_force(None, None, None, None) == binding.FPM_EINVAL
     assert libfpm.fpm_kdk(None, None, None, None, 1, None, None, None) == binding.FPM_EINVAL
     assert libfpm.fpm_status(None, None) == binding.FPM_EINVAL
+    assert libfpm.fpm_kdk_adj(None, None, None, None, 1, None, None, None, None) == binding.FPM_EINVAL
+    assert libfpm.fpm_set_force_kernel(None, binding.GREENS["discrete"], binding.GRADIENTS["exact"]) == binding.FPM_EINVAL
+    assert libfpm.fpm_set_pyramid(None, 2, 2, 16) == binding.FPM_EINVAL
+    assert libfpm.fpm_adam_step(None, None, None, None, None, 8, 1.0, 1.0, 0.01, 0.9, 0.999, 1e-8, 1, None,
+                                None) == binding.FPM_EINVAL
     libfpm.fpm_plan_destroy(None)
 
 
