@@ -37,7 +37,7 @@ UNIT = "particle-steps/s"
 def _alg_bytes(cls, N, M, nc):
     h = 8.0 * (nc // 2 + 1) / nc            # bytes per cell of a half spectrum
     table = {
-        "kdk_readout_kick_drift": 24 + 24 + 4 + 12 * M / N,   # dx,p r/w, key w, F read
+        "kdk_readout_kick_drift": 24 + 24 + 12 * M / N,       # dx,p r/w, F read (keys: build overhead)
         "cell_keys": 12 + 4,
         "tile_scan": 0.0,
         "tile_scatter": 4 + 4,                         # key read, item write
@@ -55,6 +55,15 @@ def _alg_bytes(cls, N, M, nc):
     }
     v = table.get(cls)
     return None if v is None else v * N
+
+
+# The same, counting what the implementation's structure adds on top of the
+# method's bytes (not the roofline's numerator): the readout also writes the
+# next cell keys (4 B/particle) and reads the force mesh as float4 (16 B/cell).
+def _build_bytes(cls, N, M, nc):
+    if cls == "kdk_readout_kick_drift":
+        return (24 + 24 + 4 + 16 * M / N) * N
+    return _alg_bytes(cls, N, M, nc)
 
 
 def step_algorithmic_bytes(N, M):
@@ -286,7 +295,7 @@ def ncu_traffic(cls):
     return e.get("dram_bytes_per_launch_full_size")
 
 
-def measure_batched(reps=3):
+def measure_batched(reps=3, peak=None):
     """64 simulations (meshes 32/64/96/128, 16 each, own cosmologies, 10 KDK
     steps) by the persistent batched step, autotuned, against the same 64 runs
     launched one by one.  Each run starts from its own 2LPT initial state."""
@@ -331,16 +340,32 @@ def measure_batched(reps=3):
     t_one = timed(lambda: [pl.kdk(x, y, a) for pl, x, y in zip(plans, dxs, ps)])
     nps = sum(wl.np_ ** 3 for wl in wls) * wls[0].nsteps
     info = b.info()
-    return {"workload": "batch64_mixed_32_64_96_128_10step", "sims": len(wls), "kdk_steps": wls[0].nsteps,
+    alg = sum(step_algorithmic_bytes(wl.np_ ** 3, wl.nc ** 3) for wl in wls) * wls[0].nsteps
+    roof = None
+    if peak:
+        roof = {"bound": "hbm", "alg_bytes": alg, "peak": peak, "unit": "GB/s",
+                "achieved_batched": alg / (t_batch / 1e3) / 1e9, "frac_batched": alg / (t_batch / 1e3) / 1e9 / peak,
+                "achieved_one_by_one": alg / (t_one / 1e3) / 1e9, "frac_one_by_one": alg / (t_one / 1e3) / 1e9 / peak,
+                "bytes_model": "per simulation and PM step 60 B/particle + 44 B/cell"}
+    return {"roofline": roof, "workload": "batch64_mixed_32_64_96_128_10step", "sims": len(wls), "kdk_steps": wls[0].nsteps,
             "ms_per_batched_run": t_batch, "ms_per_one_by_one_run": t_one, "speedup": t_one / t_batch,
             "particle_steps_per_s_batched": nps / (t_batch / 1e3),
             "launches_per_step": 1, "graph_captured": info["graph_captured"], "grid_blocks": info["grid_blocks"],
             "autotune": tuned["config"], "autotune_cached": tuned["cached"]}
 
 
-def measure_fwd_adjoint(wl, reps=1):
+def adjoint_algorithmic_bytes(N, M, nsteps):
+    """Method bytes of a forward + adjoint run: the forward's per-step bytes
+    and, per reverse step, about twice as many (8 transforms, 3 cotangent
+    paints and the position terms), i.e. 3x the forward per PM step."""
+    return 3.0 * step_algorithmic_bytes(N, M) * nsteps
+
+
+def measure_fwd_adjoint(wl, reps=1, peak=None):
     """Forward + hand-written adjoint (d chi^2 / d white) of workload wl,
-    with dx checkpointed at every stage; ms per iteration and per PM step."""
+    with dx checkpointed at every stage; ms per iteration and per PM step,
+    the roofline fraction of the method's bytes and the per-class device
+    time of one forward + adjoint (CUDA events around each launcher)."""
     import numpy as np
     import torch
     from paper_2010_11847_gb300 import inputs
@@ -372,10 +397,24 @@ def measure_fwd_adjoint(wl, reps=1):
             fn()
         torch.cuda.synchronize()
         out[name] = 1e3 * (time.perf_counter() - t0) / reps
+    pl.profile(True)
+    fwd_adj()
+    prof = pl.profile_read()
+    pl.profile(False)
     pl.close()
-    return {"workload": wl.name, "ms_fwd": out["fwd"], "ms_fwd_adj": out["fwd_adj"],
-            "ms_per_pm_step_fwd_adj": out["fwd_adj"] / wl.nsteps, "ratio_fwd_adj_to_fwd": out["fwd_adj"] / out["fwd"],
-            "particle_steps_per_s_fwd_adj": wl.np_ ** 3 * wl.nsteps / (out["fwd_adj"] / 1e3)}
+    N, M = wl.np_ ** 3, wl.nc ** 3
+    alg = adjoint_algorithmic_bytes(N, M, wl.nsteps)
+    res = {"workload": wl.name, "ms_fwd": out["fwd"], "ms_fwd_adj": out["fwd_adj"],
+           "ms_per_pm_step_fwd_adj": out["fwd_adj"] / wl.nsteps, "ratio_fwd_adj_to_fwd": out["fwd_adj"] / out["fwd"],
+           "particle_steps_per_s_fwd_adj": N * wl.nsteps / (out["fwd_adj"] / 1e3),
+           "breakdown_fwd_adj": {k: {"ms": v[0], "launches": v[1]} for k, v in sorted(prof.items())}}
+    if peak:
+        gbs = alg / (out["fwd_adj"] / 1e3) / 1e9
+        res["roofline"] = {"bound": "hbm", "alg_bytes": alg, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                           "frac": gbs / peak,
+                           "bytes_model": "forward 60 B/particle + 44 B/cell per PM step, adjoint twice that per "
+                                          "reverse step (3x the forward in all)"}
+    return res
 
 
 def measure_force_variants(wl, reps=10):
@@ -689,9 +728,12 @@ def run_fpm(args):
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     step_ms = ms_step / pm_steps
     step_alg = step_algorithmic_bytes(N, M)
+    build = _build_bytes(dominant, N, M, wl.nc)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dominant),
-                "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
+                "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms,
+                "build_bytes_per_launch": build,
+                "build_frac": build / (per_launch_ms / 1e3) / 1e9 / peak}
     cpu = None if args.no_cpu_baseline else oracle_sample()
     extra = {}
     if not args.no_adjoint and args.workload == "large":
@@ -699,7 +741,7 @@ def run_fpm(args):
         del dx, p, rho, lin_k
         torch.cuda.empty_cache()
         from paper_2010_11847_gb300 import inputs as _in
-        extra["fwd_adjoint"] = measure_fwd_adjoint(wl)
+        extra["fwd_adjoint"] = measure_fwd_adjoint(wl, peak=peak)
         extra["reconstruction"] = measure_reconstruction()
         torch.cuda.empty_cache()
         extra["force_variants"] = measure_force_variants(wl)
@@ -709,10 +751,10 @@ def run_fpm(args):
         extra["cufft_reference"] = measure_cufft_reference()
         # the paper's reconstruction iteration (5-step 128^3, 400 Mpc/h) is this config:
         # ~1.1 s/iter on one V100 for forward + gradient + Adam (context only)
-        extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5)
+        extra["fwd_adjoint_128"] = measure_fwd_adjoint(_in.DIFFERENTIABLE, reps=5, peak=peak)
         torch.cuda.empty_cache()
     if not args.no_batch:
-        extra["batched"] = measure_batched()
+        extra["batched"] = measure_batched(peak=peak)
     breakdown = {k: {"ms_per_sim": v[0] / args.steps, "launches_per_sim": v[1] / args.steps} for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -41,3 +41,16 @@ def test_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
 def test_committed_traffic_matches_the_current_readout_sources():
     """The committed capture was taken on the readout's current code."""
     assert bench.ncu_traffic("kdk_readout_kick_drift") is not None
+
+
+def test_roofline_bytes_follow_the_method_minimum():
+    """The readout's roofline numerator is the method's 48 B/particle + 12
+    B/cell (keys and the float4 padding are build overhead, reported apart);
+    the PM step is 60 B/particle + 44 B/cell, the adjoint run 3x that."""
+    N = M = 512 ** 3
+    assert bench._alg_bytes("kdk_readout_kick_drift", N, M, 512) == 60.0 * N
+    assert bench._build_bytes("kdk_readout_kick_drift", N, M, 512) == 68.0 * N
+    assert bench.step_algorithmic_bytes(N, M) == 104.0 * N
+    assert bench.adjoint_algorithmic_bytes(N, M, 40) == 3 * 104.0 * N * 40
+    N2, M2 = 128 ** 3, 256 ** 3
+    assert bench._alg_bytes("kdk_readout_kick_drift", N2, M2, 256) == 48.0 * N2 + 12.0 * M2
