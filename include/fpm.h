@@ -291,21 +291,24 @@ int fpm_batch_status(fpm_batch* batch, void* stream);
 /* Persistent grid size in blocks, and whether the run was graph-captured. */
 int fpm_batch_info(fpm_batch* batch, int* grid_blocks, int* graph_captured);
 
-/* CIC paint that allocates nothing (the paper has no counterpart: this is a
- * service for callers that cannot call cudaMalloc -- code running while a
- * stream is captured into a CUDA graph, loops that cannot afford
- * cudaMalloc's implicit device synchronisation, hosts that own all device
- * memory).  Same result as fpm_paint without a plan: rho (float[nc^3],
- * mean 1) of np^3 particles at q + dx (dx: float[3][np^3]); both caller
- * device buffers.  Scratch is one fixed file-scope device array of about
- * 2.9 MB that every GPU loading the library keeps until exit; sizes above
- * its maximum -- np or nc larger than 64 -- are rejected with FPM_EINVAL,
- * as are unsupported sizes.  The first call on a device looks the array's
- * device address up (cudaGetSymbolAddress), so make that first call before
- * any stream capture.  All calls share the array: calls whose execution
- * overlaps on the GPU (other streams, other host threads) race and must be
+/* CIC paint that allocates nothing.  The paper has no counterpart: this is
+ * a service for callers that cannot call cudaMalloc -- hosts or plugins that
+ * hand out every byte of device memory themselves, loops that cannot afford
+ * cudaMalloc's implicit device synchronisation.  Same result as fpm_paint
+ * without a plan: rho (float[nc^3], mean 1) of np^3 particles at q + dx
+ * (dx: float[3][np^3]); both caller device buffers.  Scratch is one fixed
+ * file-scope device array of about 2.9 MB that every GPU loading the library
+ * keeps until exit; sizes above its maximum -- np or nc larger than 64 --
+ * are rejected with FPM_EINVAL, as are unsupported sizes.  Every call looks
+ * the array's device address up (cudaGetSymbolAddress, no allocation) with
+ * the caller's device current; the first call on a device may load the
+ * library's device code there, so make that first call before any stream
+ * capture.  All calls share the array and each leaves its contents behind
+ * (the call clears what must start at zero): calls whose execution overlaps
+ * on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Device-side error flags are not reported by
- * this variant.  Asynchronous on `stream`. */
+ * this variant: a non-finite or absurdly large displacement gives an
+ * undefined density.  Asynchronous on `stream`. */
 int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream);
 
 /* Kernel classes of the per-class timing below. */

@@ -1,23 +1,21 @@
 // noalloc.cu -- a CIC paint that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being
-// captured into a CUDA graph (the runtime rejects allocation calls that are
-// not stream-ordered during a global-mode capture), latency-critical loops
-// in which cudaMalloc's implicit device synchronisation is not acceptable,
-// and host applications or plugins that hand out every byte of device
-// memory themselves.  fpm_paint_noalloc serves them: it runs the same
-// deterministic sort-and-paint kernels as fpm_paint, but its scratch (cell
-// keys, tile buckets, tile counters, the paint's tile-face partial sums and
-// the error flag) lives in one file-scope __device__ array of fixed size,
-// NOALLOC_SCRATCH_BYTES, that every GPU which loads the library holds until
-// the process exits.
+// Some callers cannot call cudaMalloc: host applications or plugins that
+// hand out every byte of device memory themselves (a fixed budget or their
+// own pool), and latency-critical loops in which cudaMalloc's implicit
+// device synchronisation is not acceptable.  fpm_paint_noalloc serves them:
+// it runs the same deterministic sort-and-paint kernels as fpm_paint, but
+// its scratch (cell keys, tile buckets, tile counters, the paint's
+// tile-face partial sums and the error flag) lives in one file-scope
+// __device__ array of fixed size, NOALLOC_SCRATCH_BYTES, that every GPU
+// which loads the library holds until the process exits.
 //
-// The array's name is only a host-side stand-in in host code, so the device
-// address is fetched once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on that device.
+// In host code the array's name is only a host-side stand-in, not a device
+// address: each call looks the device address up with cudaGetSymbolAddress
+// (a lookup that allocates nothing) with the caller's device current, so the
+// address is right on every device and after a device reset.  The first
+// call on a device may load the library's device code there.
 #include "internal.h"
-
-#include <mutex>
 
 namespace fpm {
 
@@ -39,27 +37,14 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_FLAGS + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-unsigned char* g_dev_ptr[MAX_DEVICES] = {};
-
 // Device address of the scratch array on the current device.
 int scratch_address(unsigned char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
     cudaGetLastError();
     return FPM_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return FPM_ECUDA;
-    }
-    g_dev_ptr[dev] = static_cast<unsigned char*>(ptr);
-  }
-  *out = g_dev_ptr[dev];
+  *out = static_cast<unsigned char*>(ptr);
   return FPM_OK;
 }
 }  // namespace
