@@ -464,9 +464,12 @@ def measure_force_variants(wl, reps=10):
 def measure_pyramid(levels=2, split=2, halo=16):
     """The multi-grid pyramid force (Algorithms 2-3) against the plain force
     in the accuracy configuration (128^3 on 128^3, 400 Mpc/h, 10 KDK steps
-    from 1LPT at a = 0.1): residual of the final density contrast, transfer
-    function and cross-correlation of the two, and the cost of one force
-    evaluation (CUDA events) here and on the 512^3 mesh."""
+    from 1LPT at a = 0.1), for each reading of Algorithm 3 (band-pass per
+    padded block or on the assembled mesh; coarse operator matched to the
+    fine mesh or Eq. 5 in coarse cells): residual of the final density
+    contrast, transfer function and cross-correlation of the two (Eqs.
+    10-11), and the cost of one force evaluation (CUDA events) here and on
+    the 512^3 mesh with the default reading."""
     import math
     import numpy as np
     import torch
@@ -489,30 +492,37 @@ def measure_pyramid(levels=2, split=2, halo=16):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    out, delta = {}, {}
-    for name, cfg in (("plain", (0, 0, 0)), ("pyramid", (levels, split, halo))):
-        pl.set_pyramid(*cfg)
+    def final_delta():
         dx, p = dx0.clone(), p0.clone()
         pl.kdk(dx, p, stages)
-        delta[name] = pl.paint(dx) - 1.0
-        rho = delta[name] + 1.0
-        out[f"ms_force_{name}"] = timed(lambda: pl.force(rho), 10)
-        assert pl.status() == 0
-    dp, dm = delta["pyramid"], delta["plain"]
-    k, pa, _ = pl.power(dp)
-    _, pb, _ = pl.power(dm)
-    _, pab, _ = pl.power(dp, dm)
-    tf = np.sqrt(pa / pb)
-    rc = pab / np.sqrt(pa * pb)
+        return pl.paint(dx) - 1.0
+
+    pl.set_pyramid(0)
+    dm = final_delta()
+    rho_m = dm + 1.0
+    out = {"workload": wl.name, "levels": levels, "split": split, "halo": halo,
+           "block_mesh": wl.nc // split + 2 * halo, "coarse_mesh": wl.nc >> levels,
+           "ms_force_plain": timed(lambda: pl.force(rho_m), 10), "readings": {}}
+    k, pb, _ = pl.power(dm)
     low = k < 0.5 * math.pi * wl.nc / wl.box
-    out.update({"workload": wl.name, "levels": levels, "split": split, "halo": halo,
-                "block_mesh": wl.nc // split + 2 * halo, "coarse_mesh": wl.nc >> levels,
-                "field_residual_rms": float((dp - dm).pow(2).mean().sqrt() / dm.pow(2).mean().sqrt()),
-                "projected_residual_rms": float((dp - dm).sum(2).pow(2).mean().sqrt() / dm.sum(2).pow(2).mean().sqrt()),
-                "max_abs_tf_minus_1": float(np.abs(tf - 1).max()),
-                "max_abs_tf_minus_1_below_half_nyquist": float(np.abs(tf[low] - 1).max()),
-                "max_1_minus_rc": float((1 - rc).max()),
-                "max_1_minus_rc_below_half_nyquist": float((1 - rc[low]).max())})
+    for bandpass, kernel in (("block", "matched"), ("global", "coarse"), ("block", "coarse"), ("global", "matched")):
+        pl.set_pyramid_reading(bandpass, kernel)
+        pl.set_pyramid(levels, split, halo)
+        dp = final_delta()
+        assert pl.status() == 0
+        _, pa, _ = pl.power(dp)
+        _, pab, _ = pl.power(dp, dm)
+        tf = np.sqrt(pa / pb)
+        rc = pab / np.sqrt(pa * pb)
+        out["readings"][f"{bandpass}/{kernel}"] = {
+            "ms_force_pyramid": timed(lambda: pl.force(rho_m), 10),
+            "field_residual_rms": float((dp - dm).pow(2).mean().sqrt() / dm.pow(2).mean().sqrt()),
+            "projected_residual_rms": float((dp - dm).sum(2).pow(2).mean().sqrt() / dm.sum(2).pow(2).mean().sqrt()),
+            "max_abs_tf_minus_1": float(np.abs(tf - 1).max()),
+            "max_abs_tf_minus_1_below_half_nyquist": float(np.abs(tf[low] - 1).max()),
+            "max_1_minus_rc": float((1 - rc).max()),
+            "max_1_minus_rc_below_half_nyquist": float((1 - rc[low]).max())}
+        pl.set_pyramid(0)
     pl.close()
     big = inputs.LARGE
     pb_ = Plan(128, big.nc, big.box, big.cosmo)
@@ -520,7 +530,8 @@ def measure_pyramid(levels=2, split=2, halo=16):
     out["ms_force_plain_512"] = timed(lambda: pb_.force(rho), 5)
     pb_.set_pyramid(2, 4, 32)
     out["ms_force_pyramid_512"] = timed(lambda: pb_.force(rho), 5)
-    out["pyramid_512"] = {"levels": 2, "split": 4, "halo": 32, "block_mesh": 192, "coarse_mesh": 128}
+    out["pyramid_512"] = {"levels": 2, "split": 4, "halo": 32, "block_mesh": 192, "coarse_mesh": 128,
+                          "reading": "block/matched"}
     pb_.close()
     return out
 

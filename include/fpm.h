@@ -135,17 +135,36 @@ int fpm_set_force_kernel(fpm_plan* plan, int green, int gradient);
  * F = EXPAND(F_L) + F_S - EXPAND(REDUCE(F_S)) with REDUCE = `levels`
  * stride-2 convolutions with the order-6 discrete B-spline (binomial
  * weights C(6, j)/64, periodic), EXPAND = the transposed convolutions with
- * 8 times that kernel, F_L = 2^levels x the force of REDUCE(rho - 1) on the
- * (nc >> levels)^3 mesh, F_S the force of local FFTs: split^3 cubic blocks
- * of nc/split cells, each padded by `halo` cells of its periodic neighbours
- * and transformed as a periodic mesh of B = nc/split + 2 halo cells, its
- * interior kept.  Both meshes use the default kernel (naive Green's
- * function, Eq. 5 gradient).  Requires levels in {1, 2}, nc >> levels and
- * B among the FFT sizes (16, 32, 48, 64, 96, 128, 192, 256, 384, 512),
- * split | nc.  Synchronises the device; allocates about 9 nc^3 floats.
- * Errors: FPM_EINVAL, FPM_ENOMEM.  With a pyramid set, the adjoint entry
- * points and fpm_batch_create return FPM_ENOTIMPL. */
+ * 8 times that kernel, F_L the force of REDUCE(rho - 1) on the
+ * (nc >> levels)^3 mesh in fine-cell units, F_S the force of local FFTs:
+ * split^3 cubic blocks of nc/split cells, each padded by `halo` cells of
+ * its periodic neighbours and transformed as a periodic mesh of
+ * B = nc/split + 2 halo cells, its interior kept.  The reading of the
+ * paper's scheme is chosen by fpm_set_pyramid_reading (default: band-pass
+ * per padded block, fine-mesh operator on the coarse mesh).  Requires levels
+ * in {1, 2}, nc >> levels and B among the FFT sizes (16, 32, 48, 64, 96,
+ * 128, 192, 256, 384, 512), split | nc, and B divisible by 2^levels for the
+ * per-block band-pass.  Synchronises the device; allocates about 9 nc^3
+ * floats.  Errors: FPM_EINVAL, FPM_ENOMEM.  With a pyramid set, the adjoint
+ * entry points and fpm_batch_create return FPM_ENOTIMPL. */
 int fpm_set_pyramid(fpm_plan* plan, int levels, int split, int halo);
+
+/* Reading of Algorithm 3 used by the plan's pyramid force (the paper leaves
+ * both open; Sec. 3.1, Sec. 6.1).  bandpass: FPM_PYR_BANDPASS_BLOCK applies
+ * F_S - EXPAND(REDUCE(F_S)) to each padded block's force (REDUCE and EXPAND
+ * periodic on the block) before its interior is kept; FPM_PYR_BANDPASS_GLOBAL
+ * applies it to the assembled short-range mesh.  coarse_kernel:
+ * FPM_PYR_KERNEL_MATCHED gives the coarse mesh the fine mesh's operator at
+ * the same wavenumber (naive Green's function, Eq. 5 gradient symbol at the
+ * fine frequency; three-field spectral passes); FPM_PYR_KERNEL_COARSE uses
+ * Eq. 5 in coarse-cell units.  Rebuilds a pyramid that is set (device
+ * synchronised).  Errors: FPM_EINVAL (unknown value, or a set pyramid whose
+ * block size the reading cannot split), FPM_ENOMEM. */
+#define FPM_PYR_BANDPASS_BLOCK 0
+#define FPM_PYR_BANDPASS_GLOBAL 1
+#define FPM_PYR_KERNEL_MATCHED 0
+#define FPM_PYR_KERNEL_COARSE 1
+int fpm_set_pyramid_reading(fpm_plan* plan, int bandpass, int coarse_kernel);
 
 /* CIC readout of three meshes at the particles: f_out[d][i] =
  * sum_c W(q_i + dx_i - c) F[d][c].  F: float[3][nc^3]; f_out float[3][np^3]. */

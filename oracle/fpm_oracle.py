@@ -572,12 +572,38 @@ def expand(d, levels=2, order=6):
     return d
 
 
-def local_force(rho, omega_m, split, halo):
+def coarse_force(D, omega_m, scale, kernel="matched"):
+    """Force meshes, in fine-cell units, of the density contrast D on a
+    coarse mesh whose cells are `scale` fine cells (Algorithm 3's ForceGrids
+    on the REDUCEd mesh).  kernel="coarse": Eq. 3-5's operator in coarse-cell
+    units (naive Green's function, Eq. 5's gradient with w the coarse-mesh
+    frequency), times `scale`.  kernel="matched": the fine mesh's operator at
+    the same physical wavenumber, i g(w/scale) / (w/scale)^2 with w the
+    coarse-mesh frequency, so that the coarse force of a REDUCEd field is the
+    REDUCEd fine force (up to aliasing)."""
+    if kernel == "coarse":
+        return scale * force_from_delta(D, omega_m)
+    n = D.shape[0]
+    dk = _rfftn(np.asarray(D, dtype=np.float64))
+    nx, ny, nz = half_spectrum_wavenumbers(n)
+    w = [2.0 * math.pi * a / n / scale for a in (nx, ny, nz)]      # fine-mesh frequency of each mode
+    g = [np.where(np.abs(a) == n // 2, 0.0, (8.0 * np.sin(x) - np.sin(2.0 * x)) / 6.0) for a, x in zip((nx, ny, nz), w)]
+    k2 = np.broadcast_to(w[0] ** 2 + w[1] ** 2 + w[2] ** 2, dk.shape).copy()
+    k2[0, 0, 0] = 1.0
+    pot = 1.5 * omega_m * dk / k2
+    pot[0, 0, 0] = 0.0
+    return np.stack([_irfftn(1j * np.broadcast_to(g[d], dk.shape) * pot, n) for d in range(3)])
+
+
+def local_force(rho, omega_m, split, halo, bandpass=None):
     """The short-range force grids of Algorithm 3 computed with local FFTs:
     the mesh is cut into split^3 cubic blocks of m = n/split cells; each block
     is padded by `halo` cells of its periodic neighbours, its force computed
     by ``force_from_delta`` as if the padded block were periodic (its own mean
-    removed), and its m^3 interior kept."""
+    removed), and its m^3 interior kept.  With ``bandpass`` = (levels, order)
+    each padded block's force first loses its long-range band,
+    F_b - EXPAND(REDUCE(F_b)) on the (periodic) padded block, before the
+    interior is kept."""
     rho = np.asarray(rho, dtype=np.float64)
     n = rho.shape[0]
     m = n // split
@@ -588,20 +614,30 @@ def local_force(rho, omega_m, split, halo):
             for bz in range(split):
                 ix = [(np.arange(B) + b * m - halo) % n for b in (bx, by, bz)]
                 Fb = force_from_delta(rho[np.ix_(*ix)] - 1.0, omega_m)
+                if bandpass is not None:
+                    lv, od = bandpass
+                    Fb = np.stack([Fb[i] - expand(reduce(Fb[i], lv, od), lv, od) for i in range(3)])
                 inner = slice(halo, halo + m)
                 F[:, bx * m:(bx + 1) * m, by * m:(by + 1) * m, bz * m:(bz + 1) * m] = Fb[:, inner, inner, inner]
     return F
 
 
-def pyramid_force(rho, omega_m, levels=2, split=2, halo=16, order=6):
-    """Algorithm 3: long-range force on the REDUCEd mesh (coarse cells are
-    2^levels fine cells, so the coarse force is multiplied by 2^levels to be
-    in fine-cell units), short-range force from local FFTs; the expanded
-    long-range force plus the short-range force minus its own band below the
-    coarse scale (EXPAND(REDUCE(F_S)))."""
+def pyramid_force(rho, omega_m, levels=2, split=2, halo=16, order=6, bandpass="block", coarse_kernel="matched"):
+    """Algorithm 3: the long-range force on the REDUCEd mesh (``coarse_force``,
+    in fine-cell units), the short-range force from local FFTs, combined as
+    EXPAND(F_L) + F_S - EXPAND(REDUCE(F_S)).
+
+    Two readings of where the short-range band-pass F_S - EXPAND(REDUCE(F_S))
+    acts: bandpass="block" applies it to each padded block's force before
+    its interior is kept (on the local grid, as a distributed implementation
+    holds it with its halo); bandpass="global" applies it to the assembled
+    short-range mesh.  coarse_kernel selects ``coarse_force``'s operator."""
     rho = np.asarray(rho, dtype=np.float64)
     D = reduce(rho - 1.0, levels, order)
-    FL = (2.0 ** levels) * force_from_delta(D, omega_m)
+    FL = coarse_force(D, omega_m, 2.0 ** levels, coarse_kernel)
+    if bandpass == "block":
+        FS = local_force(rho, omega_m, split, halo, bandpass=(levels, order))
+        return np.stack([expand(FL[i], levels, order) + FS[i] for i in range(3)])
     FS = local_force(rho, omega_m, split, halo)
     F = np.empty_like(FS)
     for i in range(3):

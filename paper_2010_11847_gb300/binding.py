@@ -26,10 +26,12 @@ EXPORTS = [
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
     "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
     "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
-    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step", "fpm_set_force_kernel", "fpm_set_pyramid",
+    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step", "fpm_set_force_kernel", "fpm_set_pyramid", "fpm_set_pyramid_reading",
 ]
 GREENS = {"naive": 0, "discrete": 1}     # FPM_GREEN_NAIVE, FPM_GREEN_DISCRETE (Eq. 4)
 GRADIENTS = {"fd4": 0, "exact": 1}       # FPM_GRAD_FD4 (Eq. 5), FPM_GRAD_EXACT
+PYR_BANDPASS = {"block": 0, "global": 1}
+PYR_KERNEL = {"matched": 0, "coarse": 1}
 FPM_K_COUNT = 20
 
 
@@ -80,6 +82,7 @@ def lib() -> ctypes.CDLL:
     L.fpm_adam_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64, d, d, d, d, d, d, ctypes.c_int, vp, vp]
     L.fpm_set_force_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.fpm_set_pyramid.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.fpm_set_pyramid_reading.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.fpm_paint_adj.argtypes = [vp, vp, vp, vp, vp]
     L.fpm_readout_adj.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_force_adj.argtypes = [vp, vp, vp, vp]
@@ -206,6 +209,14 @@ class Plan:
         """Multi-grid pyramid force (Algorithm 3) for later force evaluations;
         levels=0 switches it off."""
         _check("fpm_set_pyramid", lib().fpm_set_pyramid(self._h, int(levels), int(split), int(halo)))
+
+    def set_pyramid_reading(self, bandpass="block", coarse_kernel="matched"):
+        """Reading of Algorithm 3 for the pyramid force: the short-range
+        band-pass on each padded "block" or on the assembled ("global") mesh,
+        and the coarse mesh's operator "matched" to the fine mesh or Eq. 5 in
+        "coarse" cell units."""
+        _check("fpm_set_pyramid_reading", lib().fpm_set_pyramid_reading(
+            self._h, PYR_BANDPASS[bandpass], PYR_KERNEL[coarse_kernel]))
 
     def force(self, rho, F=None, stream=None):
         F = F if F is not None else self._empty(3, self.nc, self.nc, self.nc)

@@ -45,6 +45,8 @@ struct fpm_plan {
   bool own_tf = false;
   int green = FPM_GREEN_NAIVE, grad = FPM_GRAD_FD4;
   Pyramid* pyr = nullptr;      // multi-grid force (Algorithm 3) when set
+  int pyr_block = 1;           // its reading: band-pass per padded block (else on the assembled F_S)
+  int pyr_matched = 1;         // and the fine mesh's operator on the coarse mesh (else coarse-cell Eq. 5)
   bool f4 = false;             // internal force meshes interleaved (float4 per cell)
   size_t specmax = 0;          // complex elements of one half spectrum
   float2* spec = nullptr;      // 6 half spectra
@@ -477,12 +479,12 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   });
 }
 
-int fpm_set_pyramid(fpm_plan* p, int levels, int split, int halo) {
-  if (!p || levels < 0) return FPM_EINVAL;
+static int set_pyramid_impl(fpm_plan* p, int levels, int split, int halo) {
   if (levels > 0) {
     const int nco = levels <= 2 ? p->nc >> levels : 0;
+    const int B = p->nc / (split > 0 ? split : 1) + 2 * halo;
     if (levels > 2 || split < 1 || halo < 0 || p->nc % split != 0 || (nco << levels) != p->nc ||
-        !size_ok(nco) || !size_ok(p->nc / split + 2 * halo))
+        !size_ok(nco) || !size_ok(B) || (p->pyr_block && B % (1 << levels) != 0))
       return FPM_EINVAL;
   }
   FPM_CUDA_TRY(cudaDeviceSynchronize());
@@ -493,7 +495,7 @@ int fpm_set_pyramid(fpm_plan* p, int levels, int split, int halo) {
   }
   if (levels == 0) return FPM_OK;
   Pyramid* y = new Pyramid();
-  const int rc = pyramid_create(y, p->nc, levels, split, halo);
+  const int rc = pyramid_create(y, p->nc, levels, split, halo, p->pyr_block, p->pyr_matched);
   if (rc != FPM_OK) {
     pyramid_destroy(y);
     delete y;
@@ -501,6 +503,29 @@ int fpm_set_pyramid(fpm_plan* p, int levels, int split, int halo) {
   }
   p->pyr = y;
   return FPM_OK;
+}
+
+int fpm_set_pyramid(fpm_plan* p, int levels, int split, int halo) {
+  if (!p || levels < 0) return FPM_EINVAL;
+  return set_pyramid_impl(p, levels, split, halo);
+}
+
+int fpm_set_pyramid_reading(fpm_plan* p, int bandpass, int coarse_kernel) {
+  if (!p || (bandpass != FPM_PYR_BANDPASS_BLOCK && bandpass != FPM_PYR_BANDPASS_GLOBAL) ||
+      (coarse_kernel != FPM_PYR_KERNEL_MATCHED && coarse_kernel != FPM_PYR_KERNEL_COARSE))
+    return FPM_EINVAL;
+  const int block = bandpass == FPM_PYR_BANDPASS_BLOCK, matched = coarse_kernel == FPM_PYR_KERNEL_MATCHED;
+  if (block == p->pyr_block && matched == p->pyr_matched) return FPM_OK;
+  const int old_block = p->pyr_block, old_matched = p->pyr_matched;
+  p->pyr_block = block;
+  p->pyr_matched = matched;
+  if (!p->pyr) return FPM_OK;
+  const int rc = set_pyramid_impl(p, p->pyr->levels, p->pyr->split, p->pyr->halo);   // rebuilt with the reading
+  if (rc == FPM_EINVAL) {
+    p->pyr_block = old_block;
+    p->pyr_matched = old_matched;
+  }
+  return rc;
 }
 
 int fpm_set_force_kernel(fpm_plan* p, int green, int gradient) {

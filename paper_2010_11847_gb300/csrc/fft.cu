@@ -8,7 +8,7 @@
 
 namespace fpm {
 
-int fft_tables_create(FftTables* t, int n, int green, int grad) {
+int fft_tables_create(FftTables* t, int n, int green, int grad, double grad_scale) {
   t->n = n;
   std::vector<float2> tw(n);
   std::vector<float> g(n), w2(n);
@@ -19,7 +19,12 @@ int fft_tables_create(FftTables* t, int n, int green, int grad) {
     const int f = m < n / 2 ? m : m - n;            // signed frequency
     const double w = two_pi * f / n;
     if (m == n / 2) g[m] = 0.f;                                   // 0 at Nyquist either way
-    else g[m] = grad ? (float)w : (float)((8.0 * sin(w) - sin(2.0 * w)) / 6.0);   // exact, or Eq. 5
+    else if (grad) g[m] = (float)w;                               // exact
+    else if (grad_scale == 1.0) g[m] = (float)((8.0 * sin(w) - sin(2.0 * w)) / 6.0);   // Eq. 5
+    else {                                                        // Eq. 5 of a mesh grad_scale x finer
+      const double wf = w / grad_scale;
+      g[m] = (float)(grad_scale * (8.0 * sin(wf) - sin(2.0 * wf)) / 6.0);
+    }
     const double s = 2.0 * sin(0.5 * w);                          // Eq. 4: w sinc(w/2)
     w2[m] = (float)(green ? s * s : w * w);
   }

@@ -49,7 +49,9 @@ int launch_factors(const double* d_pts, int nsteps, double om, double* d_raw, do
 
 // fft.cu
 // green: 0 naive w^2, 1 Eq. 4 discrete; grad: 0 Eq. 5 difference, 1 exact w.
-int fft_tables_create(FftTables* t, int n, int green = 0, int grad = 0);
+// grad_scale s != 1 (with grad 0): the gradient symbol of a mesh s times
+// finer at the same wavenumber, in this mesh's units: s g(w / s).
+int fft_tables_create(FftTables* t, int n, int green = 0, int grad = 0, double grad_scale = 1.0);
 void fft_tables_destroy(FftTables* t);
 int fft_zfwd(const FftTables& t, const float* in, float2* spec, int nf, size_t in_fs, size_t out_fs,
              cudaStream_t s);
@@ -163,6 +165,9 @@ bool batch_size_ok(int nc, int np);
 // local blocks of nc/split cells padded by `halo` (B = nc/split + 2 halo).
 struct Pyramid {
   int nc = 0, levels = 0, split = 0, halo = 0, nco = 0, m = 0, B = 0;
+  int block_bandpass = 1;           // band-pass each padded block before cropping (else the assembled F_S)
+  int matched = 1;                  // coarse force with the fine mesh's operator (else coarse-cell Eq. 5)
+  float* bco = nullptr;             // REDUCEd block force [3][(B >> levels)^3] (block band-pass)
   size_t spec_co = 0, spec_b = 0;   // complex elements of one coarse / block half spectrum
   FftTables tco, tb;                // coarse and block FFT tables (default force kernel)
   float* dco = nullptr;             // coarse density contrast, nco^3
@@ -172,11 +177,11 @@ struct Pyramid {
   float2* sb = nullptr;             // 3 block half spectra
   float* Fb = nullptr;              // block force [3][B^3]
   float* FS = nullptr;              // short-range force [3][nc^3]
-  float* ping = nullptr;            // resampling scratch, 3 nc^3 / 2 each
+  float* ping = nullptr;            // resampling scratch, 3 max(nc^3, B^3) / 2 each
   float* pong = nullptr;
   int64_t bytes = 0;
 };
-int pyramid_create(Pyramid* y, int nc, int levels, int split, int halo);
+int pyramid_create(Pyramid* y, int nc, int levels, int split, int halo, int block_bandpass, int matched);
 void pyramid_destroy(Pyramid* y);
 // Force meshes of rho (mean 1) by Algorithm 3: planar F[3][nc^3] or float4
 // per cell (f4); `launches` is incremented by the kernels enqueued.

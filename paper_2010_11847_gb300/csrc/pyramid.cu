@@ -3,15 +3,20 @@
 //
 // Long-range force: the density contrast is REDUCEd `levels` times (stride-2
 // convolutions with the order-6 discrete B-spline, binomial weights
-// C(6, j)/64), its force computed on the coarse mesh and multiplied by
-// 2^levels (coarse cells are 2^levels fine cells).  Short-range force: the
-// fine mesh is cut into split^3 cubic blocks, each padded by `halo` cells of
-// its periodic neighbours and treated as periodic by its own (local) FFTs;
-// the interiors form F_S.  Algorithm 3 combines
-//   F = EXPAND(F_L) + F_S - EXPAND(REDUCE(F_S)),
-// evaluated here as F = F_S + EXPAND(F_L - REDUCE(F_S)) (EXPAND is linear),
-// one EXPAND instead of two; the last EXPAND pass adds F_S and writes the
-// force meshes (planar or float4-interleaved).
+// C(6, j)/64) and its force computed on the coarse mesh, in fine-cell units:
+// by default with the fine mesh's operator at the same wavenumber (the
+// gradient symbol s g(w/s) of Eq. 5 at the fine frequency, s = 2^levels,
+// through the three-field spectral passes), or with Eq. 5 in coarse-cell
+// units times s.  Short-range force: the fine mesh is cut into split^3 cubic
+// blocks, each padded by `halo` cells of its periodic neighbours and treated
+// as periodic by its own (local) FFTs.  Algorithm 3 combines
+//   F = EXPAND(F_L) + F_S - EXPAND(REDUCE(F_S)).
+// By default the band-pass F_S - EXPAND(REDUCE(F_S)) acts on each padded
+// block (REDUCE and EXPAND periodic on the block) before its interior is
+// kept, and F = EXPAND(F_L) + F_S; otherwise it acts on the assembled F_S,
+// evaluated as F = F_S + EXPAND(F_L - REDUCE(F_S)) (EXPAND is linear), one
+// EXPAND instead of two.  The last EXPAND pass adds F_S and writes the force
+// meshes (planar or float4-interleaved).
 //
 // Every resampling step is one separable pass along one axis: each output
 // element reads 7 (REDUCE) or 3-4 (EXPAND) inputs along that axis, with
@@ -129,6 +134,33 @@ __global__ void __launch_bounds__(RS_THREADS) k_expand_z_final(const float* __re
   }
 }
 
+// Last EXPAND pass (along z) of a padded block's band, fused with the
+// band-pass and the crop: for the m^3 interior cells of the block (offset
+// `halo`), F_S,d = F_b,d - EXPAND(...)_d, written into F_S at (x0, y0, z0).
+// in: 3 fields [B][B][B/2]; Fb: 3 fields B^3.
+__global__ void __launch_bounds__(RS_THREADS) k_expand_z_bandpass_crop(const float* __restrict__ in, size_t in_fs,
+                                                                       const float* __restrict__ Fb,
+                                                                       float* __restrict__ FS, int n, int B, int m,
+                                                                       int halo, int x0, int y0, int z0) {
+  const size_t total = (size_t)m * m * m;
+  const size_t MB = (size_t)B * B * B, M = (size_t)n * n * n;
+  const int h = B / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % m);
+    const size_t r = e / m;
+    const int b = (int)(r % m);
+    const int a = (int)(r / m);
+    const size_t row = (size_t)(halo + a) * B + (halo + b);
+    const int kz = halo + c;
+    const size_t out = ((size_t)(x0 + a) * n + (y0 + b)) * n + (z0 + c);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float* src = in + d * in_fs + row * h;
+      FS[d * M + out] = __ldg(Fb + d * MB + row * B + kz) - expand_taps(kz, h, [&](int q) { return __ldg(src + q); });
+    }
+  }
+}
+
 // Padded block: blk[a][b][c] = rho[ox + a][oy + b][oz + c] (periodic), B^3.
 __global__ void __launch_bounds__(RS_THREADS) k_block_gather(const float* __restrict__ rho, float* __restrict__ blk,
                                                              int n, int B, int ox, int oy, int oz) {
@@ -165,13 +197,15 @@ int grid_for(size_t total) {
 }
 
 // Force meshes F[3][n^3] (planar, cell units of this mesh) of density `in`
-// with the default kernel (naive Green's function, Eq. 5 gradient); coef
+// with the kernel of tables t (naive Green's function and Eq. 5 gradient:
+// through the potential on power-of-two meshes unless `spectral`; the
+// three-field spectral passes use t's gradient symbol as it is); coef
 // = scale * 1.5 omega_m / n^3 folds the inverse-DFT normalisation and a
 // unit scale into the Green's function.
 int mesh_force(const FftTables& t, const float* in, float* F, float2* spec, size_t specmax, float coef,
-               unsigned* ctr, int* err, cudaStream_t s, int* launches) {
+               unsigned* ctr, int* err, cudaStream_t s, int* launches, bool spectral = false) {
   const size_t M = (size_t)t.n * t.n * t.n;
-  if (fft_has_potential(t.n)) {
+  if (fft_has_potential(t.n) && !spectral) {
     float* phi = reinterpret_cast<float*>(spec + specmax);
     FPM_TRY(fft_pot_forward(t, in, spec, ctr, err, s));
     FPM_TRY(fft_pot_xgreen(t, spec, coef, ctr, err, s));
@@ -225,92 +259,20 @@ int reduce_levels(const float* in, size_t in_fs, float* out, size_t out_fs, cons
   return FPM_OK;
 }
 
-}  // namespace
-
-int pyramid_create(Pyramid* y, int nc, int levels, int split, int halo) {
-  if (levels < 1 || levels > 2 || split < 1 || halo < 0 || nc % split != 0 || (nc >> levels) << levels != nc)
-    return FPM_EINVAL;
-  const int nco = nc >> levels, m = nc / split, B = m + 2 * halo;
-  if (!fft_size_ok(nco) || !fft_size_ok(B)) return FPM_EINVAL;
-  y->nc = nc;
-  y->levels = levels;
-  y->split = split;
-  y->halo = halo;
-  y->nco = nco;
-  y->m = m;
-  y->B = B;
-  y->spec_co = (size_t)nco * nco * (nco / 2 + 1);
-  y->spec_b = (size_t)B * B * (B / 2 + 1);
-  const size_t M = (size_t)nc * nc * nc, Mco = (size_t)nco * nco * nco, MB = (size_t)B * B * B;
-  FPM_TRY(fft_tables_create(&y->tco, nco));
-  FPM_TRY(fft_tables_create(&y->tb, B));
-  FPM_CUDA_TRY(cudaMalloc(&y->dco, Mco * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->sco, 3 * y->spec_co * sizeof(float2)));
-  FPM_CUDA_TRY(cudaMalloc(&y->FL, 3 * Mco * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->blk, MB * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->sb, 3 * y->spec_b * sizeof(float2)));
-  FPM_CUDA_TRY(cudaMalloc(&y->Fb, 3 * MB * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->FS, 3 * M * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->ping, 3 * (M / 2) * sizeof(float)));
-  FPM_CUDA_TRY(cudaMalloc(&y->pong, 3 * (M / 2) * sizeof(float)));
-  y->bytes = (int64_t)((Mco + 3 * Mco + MB + 3 * MB + 3 * M + 3 * M) * sizeof(float) +
-                       3 * (y->spec_co + y->spec_b) * sizeof(float2));
-  return FPM_OK;
-}
-
-void pyramid_destroy(Pyramid* y) {
-  if (y->tco.tw) fft_tables_destroy(&y->tco);
-  if (y->tb.tw) fft_tables_destroy(&y->tb);
-  cudaFree(y->dco);
-  cudaFree(y->sco);
-  cudaFree(y->FL);
-  cudaFree(y->blk);
-  cudaFree(y->sb);
-  cudaFree(y->Fb);
-  cudaFree(y->FS);
-  cudaFree(y->ping);
-  cudaFree(y->pong);
-  *y = Pyramid();
-}
-
-int pyramid_force(const Pyramid& y, const float* rho, float* F, bool f4, double omega_m, unsigned* ctr, int* err,
-                  cudaStream_t s, int* launches) {
-  const int n = y.nc, nco = y.nco, B = y.B, m = y.m;
-  const size_t M = (size_t)n * n * n, Mco = (size_t)nco * nco * nco, MB = (size_t)B * B * B;
-  // long range: F_L = 2^levels * force(REDUCE(rho - 1)) on the coarse mesh
-  FPM_TRY(reduce_levels(rho, M, y.dco, Mco, nullptr, 1, n, y.levels, 1.f, y.ping, y.pong, s, launches));
-  const float coef_co = (float)((double)(1 << y.levels) * 1.5 * omega_m / (double)Mco);
-  FPM_TRY(mesh_force(y.tco, y.dco, y.FL, y.sco, y.spec_co, coef_co, ctr, err, s, launches));
-  // short range: local FFTs of the padded blocks, interiors into F_S
-  const float coef_b = (float)(1.5 * omega_m / (double)MB);
-  for (int bx = 0; bx < y.split; ++bx)
-    for (int by = 0; by < y.split; ++by)
-      for (int bz = 0; bz < y.split; ++bz) {
-        k_block_gather<<<grid_for(MB), RS_THREADS, 0, s>>>(rho, y.blk, n, B, bx * m - y.halo, by * m - y.halo,
-                                                           bz * m - y.halo);
-        FPM_CUDA_TRY(cudaGetLastError());
-        FPM_TRY(mesh_force(y.tb, y.blk, y.Fb, y.sb, y.spec_b, coef_b, ctr, err, s, launches));
-        k_block_scatter<<<dim3(grid_for((size_t)m * m * m), 3), RS_THREADS, 0, s>>>(y.Fb, y.FS, n, B, m, y.halo,
-                                                                                    bx * m, by * m, bz * m);
-        FPM_CUDA_TRY(cudaGetLastError());
-        *launches += 2;
-      }
-  // coarse difference F_L - REDUCE(F_S), written over F_L
-  FPM_TRY(reduce_levels(y.FS, M, y.FL, Mco, y.FL, 3, n, y.levels, 0.f, y.ping, y.pong, s, launches));
-  // EXPAND it back; the last pass adds F_S and writes F
-  int d[3] = {nco, nco, nco};
-  const float* cur = y.FL;
-  size_t cur_fs = Mco;
-  float* bufs[2] = {y.ping, y.pong};
+// `levels` EXPANDs of 3 fields of n^3 (stride in_fs) but the last pass
+// (along z), which `last(cur, cur_fs)` enqueues on the [N][N][N/2] fields.
+template <typename Last>
+int expand_levels(const float* in, size_t in_fs, int n, int levels, float* ping, float* pong, cudaStream_t s,
+                  int* launches, Last last) {
+  int d[3] = {n, n, n};
+  const float* cur = in;
+  size_t cur_fs = in_fs;
+  float* bufs[2] = {ping, pong};
   int which = 0;
-  for (int l = 0; l < y.levels; ++l) {
+  for (int l = 0; l < levels; ++l) {
     for (int ax = 0; ax < 3; ++ax) {
-      if (l == y.levels - 1 && ax == 2) {
-        if (f4)
-          k_expand_z_final<true><<<grid_for(M), RS_THREADS, 0, s>>>(cur, cur_fs, y.FS, F, n);
-        else
-          k_expand_z_final<false><<<grid_for(M), RS_THREADS, 0, s>>>(cur, cur_fs, y.FS, F, n);
-        FPM_CUDA_TRY(cudaGetLastError());
+      if (l == levels - 1 && ax == 2) {
+        FPM_TRY(last(cur, cur_fs));
         ++*launches;
         return FPM_OK;
       }
@@ -334,6 +296,115 @@ int pyramid_force(const Pyramid& y, const float* rho, float* F, bool f4, double 
     }
   }
   return FPM_OK;
+}
+
+}  // namespace
+
+int pyramid_create(Pyramid* y, int nc, int levels, int split, int halo, int block_bandpass, int matched) {
+  if (levels < 1 || levels > 2 || split < 1 || halo < 0 || nc % split != 0 || (nc >> levels) << levels != nc)
+    return FPM_EINVAL;
+  const int nco = nc >> levels, m = nc / split, B = m + 2 * halo;
+  if (!fft_size_ok(nco) || !fft_size_ok(B)) return FPM_EINVAL;
+  if (block_bandpass && (B % (1 << levels) != 0)) return FPM_EINVAL;
+  y->block_bandpass = block_bandpass ? 1 : 0;
+  y->matched = matched ? 1 : 0;
+  y->nc = nc;
+  y->levels = levels;
+  y->split = split;
+  y->halo = halo;
+  y->nco = nco;
+  y->m = m;
+  y->B = B;
+  y->spec_co = (size_t)nco * nco * (nco / 2 + 1);
+  y->spec_b = (size_t)B * B * (B / 2 + 1);
+  const size_t M = (size_t)nc * nc * nc, Mco = (size_t)nco * nco * nco, MB = (size_t)B * B * B;
+  FPM_TRY(fft_tables_create(&y->tco, nco, 0, 0, matched ? (double)(1 << levels) : 1.0));
+  FPM_TRY(fft_tables_create(&y->tb, B));
+  FPM_CUDA_TRY(cudaMalloc(&y->dco, Mco * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&y->sco, 3 * y->spec_co * sizeof(float2)));
+  FPM_CUDA_TRY(cudaMalloc(&y->FL, 3 * Mco * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&y->blk, MB * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&y->sb, 3 * y->spec_b * sizeof(float2)));
+  FPM_CUDA_TRY(cudaMalloc(&y->Fb, 3 * MB * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&y->FS, 3 * M * sizeof(float)));
+  const size_t half = (M > MB ? M : MB) / 2;
+  const int Bco = B >> levels;
+  const size_t MBco = block_bandpass ? (size_t)Bco * Bco * Bco : 0;
+  FPM_CUDA_TRY(cudaMalloc(&y->ping, 3 * half * sizeof(float)));
+  FPM_CUDA_TRY(cudaMalloc(&y->pong, 3 * half * sizeof(float)));
+  if (block_bandpass) FPM_CUDA_TRY(cudaMalloc(&y->bco, 3 * MBco * sizeof(float)));
+  y->bytes = (int64_t)((Mco + 3 * Mco + MB + 3 * MB + 3 * M + 6 * half + 3 * MBco) * sizeof(float) +
+                       3 * (y->spec_co + y->spec_b) * sizeof(float2));
+  return FPM_OK;
+}
+
+void pyramid_destroy(Pyramid* y) {
+  if (y->tco.tw) fft_tables_destroy(&y->tco);
+  if (y->tb.tw) fft_tables_destroy(&y->tb);
+  cudaFree(y->dco);
+  cudaFree(y->sco);
+  cudaFree(y->FL);
+  cudaFree(y->blk);
+  cudaFree(y->sb);
+  cudaFree(y->Fb);
+  cudaFree(y->FS);
+  cudaFree(y->ping);
+  cudaFree(y->pong);
+  cudaFree(y->bco);
+  *y = Pyramid();
+}
+
+int pyramid_force(const Pyramid& y, const float* rho, float* F, bool f4, double omega_m, unsigned* ctr, int* err,
+                  cudaStream_t s, int* launches) {
+  const int n = y.nc, nco = y.nco, B = y.B, m = y.m;
+  const size_t M = (size_t)n * n * n, Mco = (size_t)nco * nco * nco, MB = (size_t)B * B * B;
+  const int Bco = B >> y.levels;
+  const size_t MBco = (size_t)Bco * Bco * Bco;
+  // long range: F_L = force(REDUCE(rho - 1)) on the coarse mesh, in fine-cell
+  // units (the 2^levels of coarse-cell units folded into coef; with matched
+  // tables it pairs with their s g(w/s) to give the fine operator)
+  FPM_TRY(reduce_levels(rho, M, y.dco, Mco, nullptr, 1, n, y.levels, 1.f, y.ping, y.pong, s, launches));
+  const float coef_co = (float)((double)(1 << y.levels) * 1.5 * omega_m / (double)Mco);
+  FPM_TRY(mesh_force(y.tco, y.dco, y.FL, y.sco, y.spec_co, coef_co, ctr, err, s, launches, y.matched != 0));
+  // short range: local FFTs of the padded blocks, interiors into F_S
+  const float coef_b = (float)(1.5 * omega_m / (double)MB);
+  for (int bx = 0; bx < y.split; ++bx)
+    for (int by = 0; by < y.split; ++by)
+      for (int bz = 0; bz < y.split; ++bz) {
+        k_block_gather<<<grid_for(MB), RS_THREADS, 0, s>>>(rho, y.blk, n, B, bx * m - y.halo, by * m - y.halo,
+                                                           bz * m - y.halo);
+        FPM_CUDA_TRY(cudaGetLastError());
+        ++*launches;
+        FPM_TRY(mesh_force(y.tb, y.blk, y.Fb, y.sb, y.spec_b, coef_b, ctr, err, s, launches));
+        if (y.block_bandpass) {
+          // F_b - EXPAND(REDUCE(F_b)) on the periodic padded block, interior into F_S
+          FPM_TRY(reduce_levels(y.Fb, MB, y.bco, MBco, nullptr, 3, B, y.levels, 0.f, y.ping, y.pong, s, launches));
+          FPM_TRY(expand_levels(y.bco, MBco, Bco, y.levels, y.ping, y.pong, s, launches,
+                                [&](const float* cur, size_t cur_fs) {
+                                  k_expand_z_bandpass_crop<<<grid_for((size_t)m * m * m), RS_THREADS, 0, s>>>(
+                                      cur, cur_fs, y.Fb, y.FS, n, B, m, y.halo, bx * m, by * m, bz * m);
+                                  FPM_CUDA_TRY(cudaGetLastError());
+                                  return FPM_OK;
+                                }));
+        } else {
+          k_block_scatter<<<dim3(grid_for((size_t)m * m * m), 3), RS_THREADS, 0, s>>>(y.Fb, y.FS, n, B, m, y.halo,
+                                                                                      bx * m, by * m, bz * m);
+          FPM_CUDA_TRY(cudaGetLastError());
+          ++*launches;
+        }
+      }
+  // band-pass of the assembled F_S: coarse difference F_L - REDUCE(F_S), written over F_L
+  if (!y.block_bandpass)
+    FPM_TRY(reduce_levels(y.FS, M, y.FL, Mco, y.FL, 3, n, y.levels, 0.f, y.ping, y.pong, s, launches));
+  // EXPAND the coarse field back; the last pass adds F_S and writes F
+  return expand_levels(y.FL, Mco, nco, y.levels, y.ping, y.pong, s, launches, [&](const float* cur, size_t cur_fs) {
+    if (f4)
+      k_expand_z_final<true><<<grid_for(M), RS_THREADS, 0, s>>>(cur, cur_fs, y.FS, F, n);
+    else
+      k_expand_z_final<false><<<grid_for(M), RS_THREADS, 0, s>>>(cur, cur_fs, y.FS, F, n);
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  });
 }
 
 }  // namespace fpm

@@ -1,8 +1,10 @@
 """Multi-grid pyramid force (Algorithms 2-3) through the C ABI against the
 oracle's ``pyramid_force``: force meshes relative L2 <= 1e-5 for coarse and
 block meshes on both FFT paths (power-of-two potential form, shared-memory
-passes), KDK positions and momenta <= 1e-4, the off switch, and the
-refusals (bad sizes, adjoint, batch)."""
+passes) under the four readings (band-pass per padded block or on the
+assembled mesh, coarse operator matched to the fine mesh or in coarse
+cells), KDK positions and momenta <= 1e-4, the reading and off switches,
+and the refusals (bad sizes, adjoint, batch)."""
 import numpy as np
 import pytest
 
@@ -40,16 +42,22 @@ def dev(x, torch):
 CASES = [(64, 2, 2, 16), (128, 2, 2, 16), (64, 1, 4, 8), (96, 1, 2, 24), (128, 2, 4, 16)]
 
 
+READINGS = [("block", "matched"), ("global", "coarse"), ("block", "coarse"), ("global", "matched")]
+
+
+@pytest.mark.parametrize("reading", READINGS)
 @pytest.mark.parametrize("nc,levels,split,halo", CASES)
-def test_pyramid_force_matches_oracle(torch_mod, nc, levels, split, halo):
+def test_pyramid_force_matches_oracle(torch_mod, nc, levels, split, halo, reading):
     torch = torch_mod
     pl = plan(nc // 2, nc)
+    pl.set_pyramid_reading(*reading)
     pl.set_pyramid(levels, split, halo)
     rho = (1.0 + 0.5 * inputs.random_field(nc, 500 + nc)).astype(np.float32)
     F = pl.force(dev(rho, torch)).cpu().numpy()
     torch.cuda.synchronize()
     assert pl.status() == 0
-    ref = O.pyramid_force(rho.astype(np.float64), OM, levels, split, halo)
+    ref = O.pyramid_force(rho.astype(np.float64), OM, levels, split, halo, bandpass=reading[0],
+                          coarse_kernel=reading[1])
     for d in range(3):
         assert rel_l2(F[d], ref[d]) < 1e-5, (d, rel_l2(F[d], ref[d]))
 
@@ -74,6 +82,25 @@ def test_pyramid_kdk_matches_oracle(torch_mod):
     assert pl.status() == 0
     assert rel_l2(dx.cpu().numpy(), rdx) < 1e-4
     assert rel_l2(p.cpu().numpy(), rp) < 1e-4
+
+
+def test_pyramid_reading_switch_rebuilds_the_pyramid(torch_mod):
+    """Changing the reading of a set pyramid rebuilds it: the force follows
+    the new reading, and switching back gives the first bits again."""
+    torch = torch_mod
+    nc = 64
+    rho = dev((1.0 + 0.5 * inputs.random_field(nc, 530)).astype(np.float32), torch)
+    pl = plan(32, nc)
+    pl.set_pyramid(2, 2, 16)
+    a = pl.force(rho).clone()
+    pl.set_pyramid_reading("global", "coarse")
+    b = pl.force(rho).clone()
+    pl.set_pyramid_reading("block", "matched")
+    c = pl.force(rho)
+    torch.cuda.synchronize()
+    assert not torch.equal(a, b) and torch.equal(a, c)
+    ref = O.pyramid_force(rho.cpu().numpy().astype(np.float64), OM, 2, 2, 16, bandpass="global", coarse_kernel="coarse")
+    assert rel_l2(b.cpu().numpy(), ref) < 1e-5
 
 
 def test_switching_the_pyramid_off_gives_the_default_bits(torch_mod):
