@@ -310,6 +310,47 @@ int fpm_batch_status(fpm_batch* batch, void* stream);
 /* Persistent grid size in blocks, and whether the run was graph-captured. */
 int fpm_batch_info(fpm_batch* batch, int* grid_blocks, int* graph_captured);
 
+/* Per-mesh-size layout of the batched step, for every simulation of the
+ * batch whose mesh is nc (an autotuner's knobs; none changes a result bit):
+ *   FPM_BTUNE_READOUT    the fused readout's particle traversal: 0 chunks of
+ *                        consecutive particles, 1 or 2 Lagrangian bricks of
+ *                        4 x 32 x 32 or 4 x 16 x 64 particles (np divisible);
+ *   FPM_BTUNE_PAINT_TILE the paint's tile edge, 8 or 16 cells (the particles
+ *                        are bucketed and painted by tiles of that edge; 8
+ *                        gives small meshes 8x more work items);
+ *   FPM_BTUNE_FFT_SLOTS  points per thread of the power-of-two FFT passes,
+ *                        8 or 16 (16: half the threads per line, twice the
+ *                        lines per block).
+ * Invalidates the batch's captured graph.  Errors: FPM_EINVAL (no such mesh
+ * in the batch, or a value the mesh cannot take), FPM_ENOMEM. */
+#define FPM_BTUNE_READOUT 0
+#define FPM_BTUNE_PAINT_TILE 1
+#define FPM_BTUNE_FFT_SLOTS 2
+int fpm_batch_tune(fpm_batch* batch, int nc, int knob, int value);
+
+/* Device milliseconds of each phase of the batched step, accumulated over
+ * every fpm_batch_kdk since the last read, then reset: ms (HOST array of
+ * n >= FPM_BPH_COUNT entries) in the order below.  A phase's time is the
+ * first block's wall time from the end of the previous phase's grid barrier
+ * to the end of its own (every block has then finished it); the last phase
+ * of a launch ends when the first block finishes it.  Synchronises
+ * `stream`.  Errors: FPM_EINVAL, FPM_ECUDA. */
+#define FPM_BPH_KEYS 0      /* cell keys of the initial state          */
+#define FPM_BPH_KDK 1       /* readout + kick + drift + keys            */
+#define FPM_BPH_SCAN 2      /* tile-count scan                          */
+#define FPM_BPH_SCATTER 3   /* bucketing by tile                        */
+#define FPM_BPH_PAINT 4     /* tile paint                               */
+#define FPM_BPH_HALO 5      /* tile-face sums                           */
+#define FPM_BPH_ZF 6        /* z r2c                                    */
+#define FPM_BPH_YF 7        /* y forward                                */
+#define FPM_BPH_X 8         /* x pass with the Green's function         */
+#define FPM_BPH_YI 9        /* y inverse                                */
+#define FPM_BPH_ZI 10       /* z c2r                                    */
+#define FPM_BPH_GRAD 11     /* Eq. 5 difference of the potential        */
+#define FPM_BPH_KDK_LAST 12 /* closing kick                             */
+#define FPM_BPH_COUNT 13
+int fpm_batch_phase_times(fpm_batch* batch, double* ms, int n, void* stream);
+
 /* CIC paint that allocates nothing.  The paper has no counterpart: this is
  * a service for callers that cannot call cudaMalloc -- hosts or plugins that
  * hand out every byte of device memory themselves, loops that cannot afford
@@ -356,7 +397,10 @@ int fpm_paint_noalloc(int np, int nc, const float* dx, float* rho, void* stream)
 
 /* Turn per-kernel-class timing on or off for this plan (off by default).
  * When on, every launch of the plan is bracketed by CUDA events recorded on
- * the launching stream; this adds no synchronisation. */
+ * the launching stream; this adds no synchronisation.  enable: 0 off, 1
+ * every class; FPM_PROFILE_ONLY(cls) times the launches of class cls only
+ * (two events per such launch, the rest of the plan's work untouched). */
+#define FPM_PROFILE_ONLY(cls) (2 + (cls))
 int fpm_profile(fpm_plan* plan, int enable);
 
 /* Synchronise `stream`, then return the accumulated device milliseconds and

@@ -26,11 +26,14 @@ EXPORTS = [
     "fpm_profile", "fpm_profile_read", "fpm_kernel_class_name", "fpm_launch_count", "fpm_paint_noalloc",
     "fpm_chi2", "fpm_paint_adj", "fpm_readout_adj", "fpm_force_adj", "fpm_kdk_adj", "fpm_lpt_adj",
     "fpm_linear_field_adj", "fpm_batch_create", "fpm_batch_destroy", "fpm_batch_configure", "fpm_batch_kdk",
-    "fpm_batch_status", "fpm_batch_info", "fpm_adam_step", "fpm_set_force_kernel", "fpm_set_pyramid", "fpm_set_pyramid_reading",
+    "fpm_batch_status", "fpm_batch_info", "fpm_batch_phase_times", "fpm_batch_tune", "fpm_adam_step", "fpm_set_force_kernel", "fpm_set_pyramid", "fpm_set_pyramid_reading",
 ]
 GREENS = {"naive": 0, "discrete": 1}     # FPM_GREEN_NAIVE, FPM_GREEN_DISCRETE (Eq. 4)
 GRADIENTS = {"fd4": 0, "exact": 1}       # FPM_GRAD_FD4 (Eq. 5), FPM_GRAD_EXACT
 PYR_BANDPASS = {"block": 0, "global": 1}
+BATCH_KNOBS = {"readout": 0, "paint_tile": 1, "fft_slots": 2}   # FPM_BTUNE_*
+BATCH_PHASES = ("keys", "kdk", "scan", "scatter", "paint", "halo", "z_r2c", "y_fwd", "x_green", "y_inv", "z_c2r",
+                "gradient", "kdk_last")     # FPM_BPH_* order
 PYR_KERNEL = {"matched": 0, "coarse": 1}
 FPM_K_COUNT = 20
 
@@ -96,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.fpm_batch_kdk.argtypes = [vp, vp, vp, vp, i, vp]
     L.fpm_batch_status.argtypes = [vp, vp]
     L.fpm_batch_info.argtypes = [vp, vp, vp]
+    L.fpm_batch_phase_times.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.fpm_batch_tune.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     for name in EXPORTS:
         if name not in ("fpm_plan_destroy", "fpm_plan_scratch_bytes", "fpm_strerror", "fpm_kernel_class_name",
                         "fpm_launch_count", "fpm_batch_destroy"):
@@ -251,8 +256,14 @@ class Plan:
     def status(self, stream=None) -> int:
         return int(lib().fpm_status(self._h, _stream(stream)))
 
-    def profile(self, enable: bool = True):
-        _check("fpm_profile", lib().fpm_profile(self._h, int(bool(enable))))
+    def profile(self, enable: bool = True, only: str = None):
+        """Per-class device timing on or off; `only` (a class name) times
+        that class's launches alone."""
+        code = int(bool(enable))
+        if enable and only is not None:
+            names = [lib().fpm_kernel_class_name(k).decode() for k in range(FPM_K_COUNT)]
+            code = 2 + names.index(only)
+        _check("fpm_profile", lib().fpm_profile(self._h, code))
 
     def profile_read(self, stream=None) -> dict:
         """{class name: (ms, launches)} accumulated since the last read."""
@@ -367,6 +378,19 @@ class Batch:
 
     def status(self, stream=None) -> int:
         return int(lib().fpm_batch_status(self._h, _stream(stream)))
+
+    def tune(self, nc: int, knob: str, value: int):
+        """Per-mesh-size layout of the batched step: knob "readout" (0 chunks,
+        1 bricks 32 in z, 2 bricks 64 in z), "paint_tile" (8 or 16) or
+        "fft_slots" (8 or 16), for every simulation of mesh nc."""
+        _check("fpm_batch_tune", lib().fpm_batch_tune(self._h, int(nc), BATCH_KNOBS[knob], int(value)))
+
+    def phase_times(self, stream=None) -> dict:
+        """{phase: device ms} accumulated over the batched runs since the last read."""
+        ms = np.zeros(len(BATCH_PHASES))
+        _check("fpm_batch_phase_times", lib().fpm_batch_phase_times(self._h, ms.ctypes.data, len(BATCH_PHASES),
+                                                                    _stream(stream)))
+        return dict(zip(BATCH_PHASES, ms.tolist()))
 
     def info(self) -> dict:
         g, c = ctypes.c_int(), ctypes.c_int()

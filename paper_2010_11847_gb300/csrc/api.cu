@@ -19,6 +19,7 @@ std::atomic<long long> g_launches{0};
 // Optional per-kernel-class timing: an event pair around each launch.
 struct Profiler {
   bool on = false;
+  int only = -1;               // >= 0: time only the launches of this class
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, size_t>> recs;   // (class, index of the start event)
@@ -60,6 +61,7 @@ struct fpm_plan {
   double* d_raw = nullptr;
   double* d_gr = nullptr;
   double* d_fac = nullptr;
+  std::vector<double> fac_pts;   // the points (stages, half stages) d_fac was computed for
   double* d_bins = nullptr;
   int* d_err = nullptr;
   int64_t scratch_bytes = 0;
@@ -169,14 +171,15 @@ int stage_points(fpm_plan* p, const double* host, int n, cudaStream_t s) {
 template <typename Fn>
 int timed(fpm_plan* p, int cls, int nk, cudaStream_t s, Fn fn) {
   size_t i0 = 0;
-  if (p->prof.on) {
+  const bool rec = p->prof.on && (p->prof.only < 0 || p->prof.only == cls);
+  if (rec) {
     i0 = p->prof.used;
     cudaEvent_t a = p->prof.next();
     if (!a || cudaEventRecord(a, s) != cudaSuccess) return FPM_ECUDA;
   }
   const int rc = fn();
   g_launches += nk;
-  if (p->prof.on) {
+  if (rec) {
     cudaEvent_t b = p->prof.next();
     if (!b || cudaEventRecord(b, s) != cudaSuccess) return FPM_ECUDA;
     p->prof.recs.push_back({cls, i0});
@@ -455,6 +458,7 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   FPM_TRY(timed(p, FPM_K_COEF, 3, s, [&] {
     return launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s);
   }));
+  p->fac_pts = pts;
   const size_t N = p->N;
   // the force of stage k is computed straight into its checkpoint slot when
   // the caller keeps them (the reverse pass then reuses it)
@@ -589,8 +593,9 @@ int fpm_power(fpm_plan* p, const float* a, const float* b, double* pk, double* k
 }
 
 int fpm_profile(fpm_plan* p, int enable) {
-  if (!p) return FPM_EINVAL;
+  if (!p || enable < 0 || enable >= 2 + FPM_K_COUNT) return FPM_EINVAL;
   p->prof.on = enable != 0;
+  p->prof.only = enable >= 2 ? enable - 2 : -1;
   p->prof.used = 0;
   p->prof.recs.clear();
   return FPM_OK;
@@ -764,6 +769,7 @@ int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const float* fckpt, const double
   FPM_TRY(timed(p, FPM_K_COEF, 3, s, [&] {
     return launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s);
   }));
+  p->fac_pts = pts;
   const size_t N3 = 3 * p->N;
   float* gp = g_p;
   if (g_p_in) {
@@ -925,9 +931,21 @@ int fpm_batch_kdk(fpm_batch* b, float* const* dx, float* const* mom, const doubl
   cudaStream_t s = S(stream);
   std::vector<double> pts(a, a + nsteps + 1);
   for (int k = 0; k < nsteps; ++k) pts.push_back(sqrt(a[k] * a[k + 1]));
-  for (fpm_plan* p : b->plans) {   // FP64 factors of every simulation's own cosmology
-    FPM_TRY(stage_points(p, pts.data(), (int)pts.size(), s));
+  // FP64 factors of every simulation's own cosmology, unless its plan
+  // already holds them for these stages; the stages are staged from the
+  // host once and copied on the device to the other plans
+  const fpm_plan* staged = nullptr;
+  for (fpm_plan* p : b->plans) {
+    if (p->fac_pts == pts) continue;
+    if (!staged) {
+      FPM_TRY(stage_points(p, pts.data(), (int)pts.size(), s));
+      staged = p;
+    } else {
+      FPM_CUDA_TRY(cudaMemcpyAsync(p->d_pts, staged->d_pts, (pts.size() + 1) * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
+    }
     FPM_TRY(launch_factors(p->d_pts, nsteps, p->cosmo.omega_m, p->d_raw, p->d_gr, p->d_fac, s));
+    p->fac_pts = pts;
     g_launches += 3;
   }
   FPM_TRY(batch_kdk(b->impl, dx, mom, nsteps, s));
@@ -946,6 +964,18 @@ int fpm_batch_status(fpm_batch* b, void* stream) {
 int fpm_batch_info(fpm_batch* b, int* grid_blocks, int* graph_captured) {
   if (!b) return FPM_EINVAL;
   return batch_info(b->impl, grid_blocks, graph_captured);
+}
+
+int fpm_batch_tune(fpm_batch* b, int nc, int knob, int value) {
+  if (!b) return FPM_EINVAL;
+  static_assert(FPM_BTUNE_READOUT == BT_READOUT && FPM_BTUNE_PAINT_TILE == BT_PAINT_TILE &&
+                    FPM_BTUNE_FFT_SLOTS == BT_FFT_SLOTS, "knob codes");
+  return batch_tune(b->impl, nc, knob, value);
+}
+
+int fpm_batch_phase_times(fpm_batch* b, double* ms, int n, void* stream) {
+  if (!b || !ms) return FPM_EINVAL;
+  return batch_phase_times(b->impl, ms, n, S(stream));
 }
 
 }  // extern "C"

@@ -48,8 +48,14 @@ struct SimDesc {
   const float2* tw;
   const float *gk, *w2;
   float force_coef;
+  int rshape;                    // readout form: 0 chunked (body_readout), 1/2 bricks of 32/64 in z
+  int te;                        // paint tile edge (16: the plan's tiles; 8: batch-owned tile tables)
+  int fv;                        // FFT slots per thread of the power-of-two passes (8 or 16)
   int items_of[NPH];
 };
+
+using Brick32 = BrickShape<32, 4, 4>;
+using Brick64 = BrickShape<64, 4, 4>;
 
 struct BatchArgs {
   const SimDesc* sims;
@@ -61,7 +67,14 @@ struct BatchArgs {
   int kind;              // 0: initial force, 1: KDK step k, 2: closing kick
   int k;                 // step index for kind 1 (closing kick of step n-1 for kind 2)
   int ro_iters;          // particle chunks of 256 per readout work item
+  unsigned long long* ptime;   // [NPH] device ns per phase (block 0's view, barrier to barrier), accumulated
 };
+
+__device__ __forceinline__ unsigned long long batch_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Bounded grid barrier (all blocks are co-resident under a cooperative
 // launch).  Returns false when this block gave up or another block already
@@ -109,16 +122,16 @@ __device__ __forceinline__ int find_sim(const int* off, int nsims, int item) {
 // Power-of-two meshes: the force through the potential, as in the
 // single-simulation path (same bodies, hence the same bits): phi in the
 // memory of the second half spectrum, then the Eq. 5 difference.
-template <int N>
+template <int N, int V>
 __device__ void fft_phase_pow2(int ph, const SimDesc& d, int local, float2* sm) {
   const int nlines = (N / 2 + 1) * N;
   float* phi = reinterpret_cast<float*>(d.spec + d.specmax);
   switch (ph) {
-    case PH_ZF: body_zfwd_r<N>(d.rho, d.spec, 0, 0, d.tw, sm, local, 0); break;
-    case PH_YF: body_yfft_r<N, false>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
-    case PH_X: body_xgreen_r<N>(d.spec, d.force_coef, d.tw, d.w2, sm, local); break;
-    case PH_YI: body_yfft_r<N, true>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
-    case PH_ZI: body_zinv_r<N>(d.spec, phi, 0, 0, d.tw, sm, local, 0); break;
+    case PH_ZF: body_zfwd_r<N, V>(d.rho, d.spec, 0, 0, d.tw, sm, local, 0); break;
+    case PH_YF: body_yfft_r<N, false, V>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
+    case PH_X: body_xgreen_r<N, V>(d.spec, d.force_coef, d.tw, d.w2, sm, local); break;
+    case PH_YI: body_yfft_r<N, true, V>(d.spec, nlines, 0, d.tw, sm, local, 0); break;
+    case PH_ZI: body_zinv_r<N, V>(d.spec, phi, 0, 0, d.tw, sm, local, 0); break;
     case PH_GRAD: {
       using SC = StCfg<N>;
       constexpr int nbz = N / SC::TZ, nby = N / SC::TY;
@@ -159,6 +172,8 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
     phases[nph++] = a.kind == 0 ? PH_KEYS : PH_KDK;
     for (int ph = PH_SCAN; ph <= PH_GRAD; ++ph) phases[nph++] = ph;
   }
+  const bool clock = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t_prev = clock ? batch_clock_ns() : 0ull;
   for (int q = 0; q < nph; ++q) {
     const int ph = phases[q];
     const int* off = a.off + ph * (a.nsims + 1);
@@ -168,7 +183,10 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
       const SimDesc& d = a.sims[s];
       const int local = item - off[s];
       switch (ph) {
-        case PH_KEYS: body_keys(d.dx, d.g, d.N, d.keys, d.tile_count, d.err, local); break;
+        case PH_KEYS:
+          if (d.te == 8) body_keys<8>(d.dx, d.g, d.N, d.keys, d.tile_count, d.err, local);
+          else body_keys<16>(d.dx, d.g, d.N, d.keys, d.tile_count, d.err, local);
+          break;
         case PH_KDK:
         case PH_KDK_LAST: {
           const bool last = ph == PH_KDK_LAST;
@@ -176,33 +194,70 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
           const int ik1 = last ? 3 * k + 2 : 3 * k, ik2 = last ? -1 : (k > 0 ? 3 * (k - 1) + 2 : -1);
           const int idr = last ? -1 : 3 * k + 1;
           uint32_t* keys = last ? nullptr : d.keys;
-          if (d.f4)
-            body_readout<true, true, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
-                                     d.tile_count, d.err, a.ro_iters, local);
-          else
-            body_readout<true, false, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
-                                      d.tile_count, d.err, a.ro_iters, local);
+          // the force mesh was written by the previous launch: read-only path
+          const float4* F4p = reinterpret_cast<const float4*>(d.F);
+          if (d.te == 8) {
+            if (d.f4 && d.rshape == 1)
+              body_kdk_brick<Brick32, 8>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+            else if (d.f4 && d.rshape == 2)
+              body_kdk_brick<Brick64, 8>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+            else if (d.f4)
+              body_readout<true, true, true, 8>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+                                                d.tile_count, d.err, a.ro_iters, local);
+            else
+              body_readout<true, false, true, 8>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+                                                 d.tile_count, d.err, a.ro_iters, local);
+          } else {
+            if (d.f4 && d.rshape == 1)
+              body_kdk_brick<Brick32>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+            else if (d.f4 && d.rshape == 2)
+              body_kdk_brick<Brick64>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+            else if (d.f4)
+              body_readout<true, true, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+                                             d.tile_count, d.err, a.ro_iters, local);
+            else
+              body_readout<true, false, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
+                                              d.tile_count, d.err, a.ro_iters, local);
+          }
           break;
         }
         case PH_SCAN: body_scan_tiles(d.tile_count, d.ntiles, d.tile_start, d.tile_cursor, su, 1); break;
-        case PH_SCATTER: body_scatter_cube<BT>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su); break;
-        case PH_PAINT:
-          body_paint_bucket_acc<true>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err,
-                                      Acc32{su, su + ACC}, local, d.cells);
+        case PH_SCATTER:
+          if (d.te == 8) body_scatter_cube<BT, 8>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su);
+          else body_scatter_cube<BT, 16>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su);
           break;
-        case PH_HALO: body_paint_halo(d.halo, d.g, d.rho, su, local); break;
+        case PH_PAINT:
+          if (d.te == 8)
+            body_paint_bucket_acc<true, Acc32, 8>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err,
+                                                  Acc32{su, su + TileC<8>::ACC}, local, d.cells);
+          else
+            body_paint_bucket_acc<true, Acc32, 16>(d.dx, d.N, d.items, d.tile_start, d.g, d.rho, d.halo, d.err,
+                                                   Acc32{su, su + TileC<16>::ACC}, local, d.cells);
+          break;
+        case PH_HALO:
+          if (d.te == 8) body_paint_halo<8>(d.halo, d.g, d.rho, su, local);
+          else body_paint_halo<16>(d.halo, d.g, d.rho, su, local);
+          break;
         default:
-          switch (d.nc) {
-            case 32: fft_phase_pow2<32>(ph, d, local, sm); break;
-            case 64: fft_phase_pow2<64>(ph, d, local, sm); break;
-            case 128: fft_phase_pow2<128>(ph, d, local, sm); break;
-            case 96: fft_phase_smem<96>(ph, d, local, sm); break;
+          switch (d.nc * 2 + (d.fv == 16)) {
+            case 64: fft_phase_pow2<32, 8>(ph, d, local, sm); break;
+            case 65: fft_phase_pow2<32, 16>(ph, d, local, sm); break;
+            case 128: fft_phase_pow2<64, 8>(ph, d, local, sm); break;
+            case 129: fft_phase_pow2<64, 16>(ph, d, local, sm); break;
+            case 256: fft_phase_pow2<128, 8>(ph, d, local, sm); break;
+            case 257: fft_phase_pow2<128, 16>(ph, d, local, sm); break;
+            case 192: case 193: fft_phase_smem<96>(ph, d, local, sm); break;
             default: break;
           }
       }
       __syncthreads();   // shared memory is reused by the next item
     }
     if (q + 1 < nph && !grid_barrier(a)) return;
+    if (clock) {   // every block has finished phase ph (past the barrier), or block 0 alone for the last
+      const unsigned long long t = batch_clock_ns();
+      atomicAdd(a.ptime + ph, t - t_prev);
+      t_prev = t;
+    }
   }
 }
 
@@ -211,17 +266,21 @@ static void items_for(SimDesc& d, int ro_iters) {
   const int nc = d.nc, nh = nc / 2 + 1, nlines = nh * nc;
   const int pchunk = BT * ro_iters;
   d.items_of[PH_KEYS] = (int)((d.N + BT - 1) / BT);
-  d.items_of[PH_KDK] = (int)((d.N + pchunk - 1) / pchunk);
+  d.items_of[PH_KDK] = d.rshape == 1 ? Brick32::blocks(d.g.np)
+                     : d.rshape == 2 ? Brick64::blocks(d.g.np) : (int)((d.N + pchunk - 1) / pchunk);
   d.items_of[PH_KDK_LAST] = d.items_of[PH_KDK];
   d.items_of[PH_SCAN] = 1;
   d.items_of[PH_SCATTER] = scatter_cube_items(d.g.np, BT);
   d.items_of[PH_PAINT] = d.ntiles;
   d.items_of[PH_HALO] = d.ntiles;
   int L = 0;
-  switch (nc) {
-    case 32: L = RegCfg<32>::L; break;
-    case 64: L = RegCfg<64>::L; break;
-    case 128: L = RegCfg<128>::L; break;
+  switch (nc * 2 + (d.fv == 16)) {
+    case 64: L = RegCfg<32>::L; break;
+    case 65: L = RegCfg<32, 16>::L; break;
+    case 128: L = RegCfg<64>::L; break;
+    case 129: L = RegCfg<64, 16>::L; break;
+    case 256: L = RegCfg<128>::L; break;
+    case 257: L = RegCfg<128, 16>::L; break;
     default: break;
   }
   if (L) {
@@ -252,6 +311,7 @@ struct Batch {
   int* d_off = nullptr;
   unsigned* d_bar = nullptr;
   int* d_status = nullptr;
+  unsigned long long* d_ptime = nullptr;   // [NPH] accumulated phase ns
   long long spin_limit = 1ll << 22;
   int blocks_per_sm = 0;      // 0: as many as fit
   int ro_iters = 1;
@@ -260,7 +320,47 @@ struct Batch {
   bool graph_ok = false;
   int graph_steps = -1;
   std::vector<float*> graph_dx, graph_p;
+  // tile tables of simulations painted by 8^3 tiles (the plan's are sized for 16^3)
+  struct Tiles8 {
+    uint32_t *count = nullptr, *start = nullptr, *cursor = nullptr;
+    unsigned long long* halo = nullptr;
+  };
+  std::vector<Tiles8> tiles8;
 };
+
+// Point simulation s at the tile tables of edge te (allocating the 8^3 ones once).
+static int set_tiles(Batch* b, int s, int te) {
+  SimDesc& d = b->host_sims[s];
+  const BatchPlanView& v = b->plans[s];
+  if (te == 16) {
+    d.te = 16;
+    d.ntiles = v.pc.ntiles;
+    d.tile_count = v.pc.tile_count;
+    d.tile_start = v.pc.tile_start;
+    d.tile_cursor = v.pc.tile_cursor;
+    d.halo = v.pc.halo;
+    return FPM_OK;
+  }
+  if (te != 8 || v.nc % 8 != 0) return FPM_EINVAL;
+  const int nt = v.nc / 8, ntiles = nt * nt * nt;
+  Batch::Tiles8& t = b->tiles8[s];
+  if (!t.count) {
+    if (cudaMalloc(&t.count, ntiles * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&t.start, (ntiles + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&t.cursor, ntiles * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&t.halo, (size_t)ntiles * TileC<8>::SHELL * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return FPM_ENOMEM;
+    }
+  }
+  d.te = 8;
+  d.ntiles = ntiles;
+  d.tile_count = t.count;
+  d.tile_start = t.start;
+  d.tile_cursor = t.cursor;
+  d.halo = t.halo;
+  return FPM_OK;
+}
 
 static int batch_grid(Batch* b) {
   int dev = 0, nsm = 0, per = 0;
@@ -301,6 +401,7 @@ static int launch_step(Batch* b, int kind, int k, cudaStream_t s) {
   a.kind = kind;
   a.k = k;
   a.ro_iters = b->ro_iters;
+  a.ptime = b->d_ptime;
   FPM_CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), s));
   void* args[] = {&a};
   FPM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_batch_step, dim3(b->grid), dim3(BT), args, BATCH_SMEM, s));
@@ -344,15 +445,22 @@ int batch_create(Batch** out, const BatchPlanView* views, int nsims) {
     d.gk = v.tab.g;
     d.w2 = v.tab.w2;
     d.force_coef = v.force_coef;
+    d.te = 16;
+    d.fv = 8;
+    d.rshape = !d.f4 ? 0 : Brick64::fits(d.g.np) ? 2 : Brick32::fits(d.g.np) ? 1 : 0;
     items_for(d, b->ro_iters);
   }
+  b->tiles8.resize(nsims);
   if (cudaMalloc(&b->d_sims, nsims * sizeof(SimDesc)) != cudaSuccess ||
       cudaMalloc(&b->d_off, (size_t)NPH * (nsims + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_ptime, NPH * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return fail(FPM_ENOMEM);
   }
-  if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) return fail(FPM_ECUDA);
+  if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(b->d_ptime, 0, NPH * sizeof(unsigned long long)) != cudaSuccess)
+    return fail(FPM_ECUDA);
   if ((rc = batch_grid(b)) != FPM_OK) return fail(rc);
   if ((rc = upload_tables(b)) != FPM_OK) return fail(rc);
   *out = b;
@@ -366,6 +474,13 @@ void batch_destroy(Batch* b) {
   cudaFree(b->d_off);
   cudaFree(b->d_bar);
   cudaFree(b->d_status);
+  cudaFree(b->d_ptime);
+  for (auto& t : b->tiles8) {
+    cudaFree(t.count);
+    cudaFree(t.start);
+    cudaFree(t.cursor);
+    cudaFree(t.halo);
+  }
   delete b;
 }
 
@@ -440,6 +555,51 @@ int batch_status(Batch* b, cudaStream_t s) {
   FPM_CUDA_TRY(cudaStreamSynchronize(s));
   FPM_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int), s));
   return (h & ERR_TIMEOUT) ? FPM_ETIMEOUT : FPM_OK;
+}
+
+int batch_tune(Batch* b, int nc, int knob, int value) {
+  bool any = false;
+  for (int s = 0; s < b->nsims; ++s) {     // validate first: all or nothing
+    const SimDesc& d = b->host_sims[s];
+    if (d.nc != nc) continue;
+    any = true;
+    if (knob == BT_READOUT) {
+      const bool ok = value == 0 || (d.f4 && ((value == 1 && Brick32::fits(d.g.np)) || (value == 2 && Brick64::fits(d.g.np))));
+      if (!ok) return FPM_EINVAL;
+    } else if (knob == BT_PAINT_TILE) {
+      if (value != 8 && value != 16) return FPM_EINVAL;
+    } else if (knob == BT_FFT_SLOTS) {
+      if ((value != 8 && value != 16) || !is_pow2_size(nc)) return FPM_EINVAL;
+    } else {
+      return FPM_EINVAL;
+    }
+  }
+  if (!any) return FPM_EINVAL;
+  for (int s = 0; s < b->nsims; ++s) {
+    SimDesc& d = b->host_sims[s];
+    if (d.nc != nc) continue;
+    if (knob == BT_READOUT) d.rshape = value;
+    else if (knob == BT_FFT_SLOTS) d.fv = value;
+    else FPM_TRY(set_tiles(b, s, value));
+    items_for(d, b->ro_iters);
+  }
+  FPM_TRY(upload_tables(b));
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_steps = -1;
+  }
+  return FPM_OK;
+}
+
+int batch_phase_times(Batch* b, double* ms, int n, cudaStream_t s) {
+  if (n < NPH) return FPM_EINVAL;
+  unsigned long long h[NPH];
+  FPM_CUDA_TRY(cudaMemcpyAsync(h, b->d_ptime, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FPM_CUDA_TRY(cudaStreamSynchronize(s));
+  FPM_CUDA_TRY(cudaMemsetAsync(b->d_ptime, 0, sizeof(h), s));
+  for (int k = 0; k < NPH; ++k) ms[k] = 1e-6 * (double)h[k];
+  return FPM_OK;
 }
 
 int batch_info(const Batch* b, int* grid, int* graph_captured) {

@@ -28,11 +28,16 @@ __host__ __device__ inline bool fft_size_ok(int n) {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex product with its rounding fixed by explicit fused multiply-adds,
+// so that every instantiation of a transform (any number of points per
+// thread) rounds it the same way: re = fma(ax, bx, -(ay by)), im = fma(ax, by, ay bx).
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Real scaling, rounded on its own (never fused into a later add), so that
+// its rounding does not depend on how a kernel is instantiated.
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
 // multiply by +i or -i
 __device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }

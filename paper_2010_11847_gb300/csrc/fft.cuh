@@ -54,12 +54,13 @@ struct Dft<8, INV> {
     float2 o[4] = {v[1], v[3], v[5], v[7]};
     Dft<4, INV>::run(e);
     Dft<4, INV>::run(o);
-    // w8^k = exp(-+ 2 pi i k / 8)
-    float2 o1 = INV ? make_float2(c * (o[1].x - o[1].y), c * (o[1].x + o[1].y))
-                    : make_float2(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x));
+    // w8^k = exp(-+ 2 pi i k / 8); the products are rounded on their own
+    // (never fused into the adds below), the same in every instantiation
+    float2 o1 = INV ? make_float2(__fmul_rn(c, o[1].x - o[1].y), __fmul_rn(c, o[1].x + o[1].y))
+                    : make_float2(__fmul_rn(c, o[1].x + o[1].y), __fmul_rn(c, o[1].y - o[1].x));
     float2 o2 = rot_q<INV>(o[2]);
-    float2 o3 = INV ? make_float2(-c * (o[3].x + o[3].y), c * (o[3].x - o[3].y))
-                    : make_float2(c * (o[3].y - o[3].x), -c * (o[3].x + o[3].y));
+    float2 o3 = INV ? make_float2(__fmul_rn(-c, o[3].x + o[3].y), __fmul_rn(c, o[3].x - o[3].y))
+                    : make_float2(__fmul_rn(c, o[3].y - o[3].x), __fmul_rn(-c, o[3].x + o[3].y));
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], o1);
@@ -77,9 +78,9 @@ struct Dft<3, INV> {
     const float s3 = 0.86602540378443864676f;   // sin(pi/3)
     float2 s = cadd(v[1], v[2]);
     float2 d = csub(v[1], v[2]);
-    float2 m = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+    float2 m = make_float2(v[0].x - __fmul_rn(0.5f, s.x), v[0].y - __fmul_rn(0.5f, s.y));
     // forward: y1 = m - i s3 d, y2 = m + i s3 d ; inverse swaps the signs
-    float2 t = make_float2(-s3 * d.y, s3 * d.x);   // i * s3 * d
+    float2 t = make_float2(__fmul_rn(-s3, d.y), __fmul_rn(s3, d.x));   // i * s3 * d
     v[0] = cadd(v[0], s);
     if (INV) {
       v[1] = cadd(m, t);

@@ -123,10 +123,10 @@ struct RegFft {
 
 __host__ __device__ constexpr bool is_pow2_size(int n) { return n >= 16 && n <= 512 && (n & (n - 1)) == 0; }
 
-// Lines per CTA: 256 threads, at least 8 lines.
-template <int N>
+// Lines per CTA: 256 threads, at least 8 lines; V slots (points) per thread.
+template <int N, int V = 8>
 struct RegCfg {
-  static constexpr int T = N / 8;
+  static constexpr int T = N / V;
   static constexpr int L = (256 / T) > 8 ? 256 / T : 8;
   static constexpr int THREADS = T * L;
   static constexpr size_t SMEM = (size_t)(L * rline<N>() + N) * sizeof(float2);
@@ -134,11 +134,11 @@ struct RegCfg {
 
 // ---------------------------------------------------------------- z r2c
 // L complex lines = 2L consecutive real rows (row = x*N + y) per CTA.
-template <int N>
+template <int N, int V = 8>
 __device__ __forceinline__ void body_zfwd_r(const float* __restrict__ in,
                                                                float2* __restrict__ out, size_t in_fs,
                                                                size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
-  using C = RegCfg<N>;
+  using C = RegCfg<N, V>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
   float2* tw = smem;
   float2* xb = tw + N;
@@ -146,14 +146,14 @@ __device__ __forceinline__ void body_zfwd_r(const float* __restrict__ in,
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   const size_t r0 = (size_t)bx * 2 * L;
   const float* src = in + by * in_fs + (r0 + 2 * g) * N;
-  float2 v[8];
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = make_float2(__ldcg(src + t + T * s), __ldcg(src + N + t + T * s));
+  for (int s = 0; s < V; ++s) v[s] = make_float2(__ldcg(src + t + T * s), __ldcg(src + N + t + T * s));
   __syncthreads();
   float2* buf = xb + g * rline<N>();
-  RegFft<N>::template run<false>(v, buf, t, tw);
+  RegFft<N, V>::template run<false>(v, buf, t, tw);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) buf[rp(t + T * s)] = v[s];
+  for (int s = 0; s < V; ++s) buf[rp(t + T * s)] = v[s];
   __syncthreads();
   float2* dst = out + by * out_fs;
   for (int idx = threadIdx.x; idx < NH * L; idx += blockDim.x) {
@@ -178,10 +178,10 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
 }
 
 // ---------------------------------------------------------------- y (in place, contiguous lines)
-template <int N, bool INV>
+template <int N, bool INV, int V = 8>
 __device__ __forceinline__ void body_yfft_r(float2* __restrict__ data, int nlines, size_t fs,
                                                                const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
-  using C = RegCfg<N>;
+  using C = RegCfg<N, V>;
   constexpr int T = C::T, L = C::L;
   float2* tw = smem;
   float2* xb = tw + N;
@@ -190,14 +190,14 @@ __device__ __forceinline__ void body_yfft_r(float2* __restrict__ data, int nline
   const int gl = bx * L + line;
   const bool valid = gl < nlines;
   float2* base = data + by * fs + (size_t)gl * N;
-  float2 v[8];
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = valid ? __ldcg(base + t + T * s) : make_float2(0.f, 0.f);
+  for (int s = 0; s < V; ++s) v[s] = valid ? __ldcg(base + t + T * s) : make_float2(0.f, 0.f);
   __syncthreads();
-  RegFft<N>::template run<INV>(v, xb + line * rline<N>(), t, tw);
+  RegFft<N, V>::template run<INV>(v, xb + line * rline<N>(), t, tw);
   if (valid) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) base[t + T * s] = v[s];
+    for (int s = 0; s < V; ++s) base[t + T * s] = v[s];
   }
 }
 
@@ -209,11 +209,11 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
 }
 
 // ---------------------------------------------------------------- z c2r
-template <int N>
+template <int N, int V = 8>
 __device__ __forceinline__ void body_zinv_r(const float2* __restrict__ in,
                                                                float* __restrict__ out, size_t in_fs,
                                                                size_t out_fs, const float2* __restrict__ g_tw, float2* smem, int bx, int by) {
-  using C = RegCfg<N>;
+  using C = RegCfg<N, V>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
   float2* tw = smem;
   float2* xb = tw + N;
@@ -236,14 +236,14 @@ __device__ __forceinline__ void body_zinv_r(const float2* __restrict__ in,
   __syncthreads();
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   float2* buf = xb + g * rline<N>();
-  float2 v[8];
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = buf[rp(t + T * s)];
+  for (int s = 0; s < V; ++s) v[s] = buf[rp(t + T * s)];
   __syncthreads();
-  RegFft<N>::template run<true>(v, buf, t, tw);
+  RegFft<N, V>::template run<true>(v, buf, t, tw);
   float* dst = out + by * out_fs + (r0 + 2 * g) * N;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < V; ++s) {
     dst[t + T * s] = v[s].x;
     dst[N + t + T * s] = v[s].y;
   }
@@ -362,10 +362,10 @@ __device__ __forceinline__ void body_xforce_r(const float2* in, float2* out, siz
 // One field in place: forward x transform of delta(k), the Green's function
 // phi = coef delta / |w|^2 (0 at k = 0, Eq. 3), inverse x transform.  The
 // Eq. 5 finite-difference gradient is then applied in real space to phi.
-template <int N>
+template <int N, int V = 8>
 __device__ __forceinline__ void body_xgreen_r(float2* data, float coef, const float2* __restrict__ g_tw,
                                               const float* __restrict__ g_w2, float2* smem, int bx) {
-  using C = RegCfg<N>;
+  using C = RegCfg<N, V>;
   constexpr int T = C::T, L = C::L, NH = N / 2 + 1;
   constexpr size_t S = (size_t)NH * N;
   float2* tw = smem;
@@ -375,22 +375,22 @@ __device__ __forceinline__ void body_xgreen_r(float2* data, float coef, const fl
   const int gl = bx * L + line;
   const bool valid = gl < NH * N;
   const int kz = gl / N, ky = gl - kz * N;
-  float2 d[8];
+  float2 d[V];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) d[s] = valid ? __ldcg(data + (size_t)(t + T * s) * S + gl) : make_float2(0.f, 0.f);
+  for (int s = 0; s < V; ++s) d[s] = valid ? __ldcg(data + (size_t)(t + T * s) * S + gl) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* buf = xb + line * rline<N>();
-  RegFft<N>::template run<false>(d, buf, t, tw);
+  RegFft<N, V>::template run<false>(d, buf, t, tw);
   const float w2yz = valid ? __ldg(g_w2 + ky) + __ldg(g_w2 + kz) : 1.f;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < V; ++s) {
     const float k2 = __ldg(g_w2 + t + T * s) + w2yz;
     d[s] = cscale(d[s], k2 > 0.f ? coef / k2 : 0.f);
   }
-  RegFft<N>::template run<true>(d, buf, t, tw);
+  RegFft<N, V>::template run<true>(d, buf, t, tw);
   if (valid) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) data[(size_t)(t + T * s) * S + gl] = d[s];
+    for (int s = 0; s < V; ++s) data[(size_t)(t + T * s) * S + gl] = d[s];
   }
 }
 

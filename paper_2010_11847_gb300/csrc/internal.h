@@ -193,6 +193,10 @@ int batch_configure(Batch* b, int blocks_per_sm, int ro_iters, long long spin_li
 int batch_kdk(Batch* b, float* const* dx, float* const* p, int nsteps, cudaStream_t s);
 int batch_status(Batch* b, cudaStream_t s);
 int batch_info(const Batch* b, int* grid, int* graph_captured);
+int batch_phase_times(Batch* b, double* ms, int n, cudaStream_t s);
+// Per-mesh-size configuration of the batched step (every simulation of mesh nc):
+enum BatchTuneKnob : int { BT_READOUT = 0, BT_PAINT_TILE = 1, BT_FFT_SLOTS = 2 };
+int batch_tune(Batch* b, int nc, int knob, int value);
 
 inline size_t spec_elems(int n) { return (size_t)n * (n / 2 + 1) * n; }
 

@@ -99,103 +99,16 @@ __global__ void __launch_bounds__(256) k_readout(float* __restrict__ dx, float* 
   body_readout<KDK, F4>(dx, p, F, g, N, M, fac, ik1, ik2, idr, f_out, keys, tile_count, err, iters, blockIdx.x);
 }
 
-// Readout + kick + drift + next key over compact Lagrangian bricks.  A CTA
-// takes a brick of KB_X x KB_Y x KB_Z lattice particles (x slowest) and
-// walks it one x plane (and half its y rows) per iteration, each warp a
-// 32-particle z segment: the force corners its particles gather lie in two
-// x planes of about (KB_Y + 1) x (KB_Z + 1) cells at a time, a window that
-// stays in L1 (a 16-byte float4 per cell) while the CTA marches through the
-// brick, so each force cell is fetched from L2 about once per brick rather
-// than once per z line.  The next iteration's dx and p are fetched (streamed,
-// evict-first) while the current one gathers.  Arithmetic and outputs are
-// those of body_readout<true, true>.  Needs np % KB_Z == 0.
-constexpr int KB_THREADS = 256;
-constexpr int KB_Z = 64;                               // z extent: KB_Z / 32 warps per row
-constexpr int KB_IPX = 4;                              // iterations per x plane
-constexpr int KB_X = 4;                                // x planes per brick
-constexpr int KB_RPI = (KB_THREADS / 32) / (KB_Z / 32);   // y rows per iteration
-constexpr int KB_Y = KB_RPI * KB_IPX;
-constexpr int KB_ITERS = KB_X * KB_IPX;
-
-__device__ __forceinline__ uint32_t brick_particle(int it, int bx, int by, int bz, int np) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int z = bz * KB_Z + (w % (KB_Z / 32)) * 32 + lane;
-  const int y = by * KB_Y + (it % KB_IPX) * KB_RPI + w / (KB_Z / 32);
-  const int x = bx * KB_X + it / KB_IPX;
-  return ((uint32_t)x * np + y) * np + z;
-}
+// Readout + kick + drift + next key over compact Lagrangian bricks
+// (body_kdk_brick): 4 x 16 x 64 particles per CTA, x slowest.
+using KdkBrick = BrickShape<64, 4, 4>;
 
 __global__ void __launch_bounds__(KB_THREADS) k_kdk_brick(float* __restrict__ dx, float* __restrict__ p,
                                                           const float4* __restrict__ F, Geom g, size_t N,
                                                           const double* __restrict__ fac, int ik1, int ik2, int idr,
                                                           uint32_t* __restrict__ keys,
                                                           uint32_t* __restrict__ tile_count, int* __restrict__ err) {
-  const int np = g.np, nc = g.nc;
-  const int nbz = np / KB_Z, nby = np / KB_Y;
-  const int bz = blockIdx.x % nbz, by = (blockIdx.x / nbz) % nby, bx = blockIdx.x / (nbz * nby);
-  const float K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
-  const float D = idr >= 0 ? (float)fac[idr] : 0.f;
-  float dn[3], pn[3];
-  {
-    const uint32_t i = brick_particle(0, bx, by, bz, np);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dn[a] = __ldcs(dx + a * N + i);
-      pn[a] = __ldcs(p + a * N + i);
-    }
-  }
-#pragma unroll 1
-  for (int it = 0; it < KB_ITERS; ++it) {
-    const uint32_t i = brick_particle(it, bx, by, bz, np);
-    float d[3] = {dn[0], dn[1], dn[2]}, pp[3] = {pn[0], pn[1], pn[2]};
-    if (it + 1 < KB_ITERS) {
-      const uint32_t inext = brick_particle(it + 1, bx, by, bz, np);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dn[a] = __ldcs(dx + a * N + inext);
-        pn[a] = __ldcs(p + a * N + inext);
-      }
-    }
-    int q[3], c[3];
-    float t[3];
-    lattice_node(i, g, q);
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-    const int cx1 = (c[0] + 1 == nc) ? 0 : c[0] + 1;
-    const int cy1 = (c[1] + 1 == nc) ? 0 : c[1] + 1;
-    const int cz1 = (c[2] + 1 == nc) ? 0 : c[2] + 1;
-    const size_t rx[2] = {(size_t)c[0] * nc * nc, (size_t)cx1 * nc * nc};
-    const int ry[2] = {c[1] * nc, cy1 * nc};
-    const int rz[2] = {c[2], cz1};
-    const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
-    float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const float4 v = __ldg(F + rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1]);
-      const float wt = wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1];
-      f[0] = fmaf(wt, v.x, f[0]);
-      f[1] = fmaf(wt, v.y, f[1]);
-      f[2] = fmaf(wt, v.z, f[2]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float pa = fmaf(K, f[a], pp[a]);
-      __stcs(p + a * N + i, pa);
-      d[a] = fmaf(D, pa, d[a]);
-      __stcs(dx + a * N + i, d[a]);
-    }
-    int tile = 0;
-    if (keys) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-      const uint32_t key = tile_key(c, g.nt);
-      keys[i] = key;
-      tile = key >> 12;
-    }
-    if (!ok) atomicOr(err, ERR_NAN);
-    if (keys) warp_count(tile_count, tile, true);
-  }
+  body_kdk_brick<KdkBrick>(dx, p, F, g, N, fac, ik1, ik2, idr, keys, tile_count, err, blockIdx.x);
 }
 
 // Paint with the permutation output: counting sort of the tile's bucket by
@@ -428,9 +341,8 @@ int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, 
   if (emit_keys) FPM_CUDA_TRY(cudaMemsetAsync(c.tile_count, 0, sizeof(uint32_t) * c.ntiles, s));
   const int it = readout_iters(c.N);
   uint32_t* keys = emit_keys ? c.keys : nullptr;
-  if (f4 && KDK_BRICK && c.g.np % KB_Z == 0 && c.g.np % KB_Y == 0 && c.g.np % KB_X == 0) {
-    const int nb = (c.g.np / KB_X) * (c.g.np / KB_Y) * (c.g.np / KB_Z);
-    k_kdk_brick<<<nb, KB_THREADS, 0, s>>>(dx, p, reinterpret_cast<const float4*>(F), c.g, c.N, fac, ik1, ik2, idr,
+  if (f4 && KDK_BRICK && KdkBrick::fits(c.g.np)) {
+    k_kdk_brick<<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, p, reinterpret_cast<const float4*>(F), c.g, c.N, fac, ik1, ik2, idr,
                                           keys, c.tile_count, c.err);
   } else if (f4)
     k_readout<true, true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr,

@@ -40,6 +40,18 @@ constexpr float W_ONE = 16777216.0f;              // 2^24: fixed-point unit of a
 constexpr float W_INV = 5.9604644775390625e-08f;  // 2^-24
 constexpr int NFACE = TILE * TILE + (TILE - 1) * TILE + (TILE - 1) * (TILE - 1);   // 721 lower-face cells
 
+// Geometry of a paint tile of edge TE (16: the cell key's tiles; 8: the
+// batched step may bucket and paint small meshes by 8^3 tiles).
+template <int TE>
+struct TileC {
+  static_assert(TE == 8 || TE == 16, "paint tile edge");
+  static constexpr int E = TE, E1 = TE + 1, E3 = TE * TE * TE, LG = TE == 8 ? 3 : 4;
+  static constexpr int ACC = E1 * E1 * E1;                                        // accumulator cells
+  static constexpr int SHELL = 2 * E1 * E1 + 2 * (E - 1) * E1 + 2 * (E - 1) * (E - 1);   // its shell
+  static constexpr int NFACE = E * E + (E - 1) * E + (E - 1) * (E - 1);            // lower-face cells
+};
+static_assert(TileC<16>::ACC == ACC && TileC<16>::SHELL == SHELL && TileC<16>::NFACE == NFACE, "16^3 tiles");
+
 // Wrap c into [0, n) for |c| < 2^31 - n (one correction in the common case).
 __device__ __forceinline__ int wrapi(int c, int n) {
   if (c < 0) c += n;
@@ -75,10 +87,13 @@ __device__ __forceinline__ bool cic_cell(float d, int q, int nc, int* c, float* 
   return true;
 }
 
+// Tile-major key of cell c with TE^3 tiles, nt = nc / TE tiles per side.
+template <int TE = 16>
 __device__ __forceinline__ uint32_t tile_key(const int* c, int nt) {
-  const uint32_t tile = ((uint32_t)(c[0] >> 4) * nt + (c[1] >> 4)) * nt + (c[2] >> 4);
-  const uint32_t local = ((c[0] & 15) * TILE + (c[1] & 15)) * TILE + (c[2] & 15);
-  return tile * TILE3 + local;
+  using C = TileC<TE>;
+  const uint32_t tile = ((uint32_t)(c[0] >> C::LG) * nt + (c[1] >> C::LG)) * nt + (c[2] >> C::LG);
+  const uint32_t local = ((c[0] & (TE - 1)) * TE + (c[1] & (TE - 1))) * TE + (c[2] & (TE - 1));
+  return tile * C::E3 + local;
 }
 
 // Warp-aggregated increment of counter[bucket] for every active lane.
@@ -91,6 +106,7 @@ __device__ __forceinline__ void warp_count(uint32_t* counter, int bucket, bool a
 }
 
 // ---------------------------------------------------------------- keys + tile histogram
+template <int TE = 16>
 __device__ __forceinline__ void body_keys(const float* __restrict__ dx, Geom g, size_t N, uint32_t* __restrict__ keys,
                                           uint32_t* __restrict__ tile_count, int* __restrict__ err, int bx) {
   const size_t i = (size_t)bx * blockDim.x + threadIdx.x;
@@ -103,9 +119,9 @@ __device__ __forceinline__ void body_keys(const float* __restrict__ dx, Geom g, 
     bool ok = true;
     for (int d = 0; d < 3; ++d) ok &= cic_cell(dx[d * N + i], q[d], g.nc, &c[d], &t);
     if (!ok) atomicOr(err, ERR_NAN);
-    const uint32_t key = tile_key(c, g.nt);
+    const uint32_t key = tile_key<TE>(c, g.nc / TE);
     keys[i] = key;
-    tile = key >> 12;
+    tile = key >> (3 * TileC<TE>::LG);
   }
   warp_count(tile_count, tile, active);
 }
@@ -179,7 +195,7 @@ __host__ __device__ inline int scatter_cube_items(int np, int threads) {
   return (np / cx) * (np / SC_CUBE) * (np / SC_CUBE);
 }
 
-template <int NT>
+template <int NT, int TE = 16>
 __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                   uint32_t* __restrict__ cursor, uint32_t* __restrict__ items,
                                                   uint16_t* __restrict__ cells, int item, uint32_t* tbl) {
@@ -207,7 +223,7 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
   uint32_t packed[SC_PER];   // slot << 16 | place in the block's range; ~0 once written directly
 #pragma unroll
   for (int e = 0; e < SC_PER; ++e) {
-    const uint32_t tile = key[e] >> 12;
+    const uint32_t tile = key[e] >> (3 * TileC<TE>::LG);
     const unsigned grp = __match_any_sync(full, tile);
     const int leader = __ffs(grp) - 1;
     int sl = -1;
@@ -228,7 +244,7 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
     const uint32_t place = __shfl_sync(full, off, leader) + __popc(grp & ((1u << lane) - 1u));
     if (sl < 0) {
       items[place] = index_of(e);
-      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
+      if (cells) cells[place] = (uint16_t)(key[e] & (TileC<TE>::E3 - 1));
       packed[e] = 0xffffffffu;
     } else {
       packed[e] = ((uint32_t)sl << 16) | place;
@@ -243,7 +259,7 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
     if (packed[e] != 0xffffffffu) {
       const uint32_t place = t_base[packed[e] >> 16] + (packed[e] & 0xffffu);
       items[place] = index_of(e);
-      if (cells) cells[place] = (uint16_t)(key[e] & (TILE3 - 1));
+      if (cells) cells[place] = (uint16_t)(key[e] & (TileC<TE>::E3 - 1));
     }
 }
 
@@ -276,35 +292,38 @@ struct Acc32 {
   __device__ __forceinline__ void zero(int c) const { lo[c] = hi[c] = 0u; }
 };
 
+template <int TE = 16>
 __device__ __forceinline__ int shell_index(int lx, int ly, int lz) {
-  // cells of the 17^3 block with a coordinate in {0, 16}
-  if (lx == 0 || lx == TILE) return (lx == TILE) * TILE1 * TILE1 + ly * TILE1 + lz;
-  if (ly == 0 || ly == TILE) return 2 * TILE1 * TILE1 + (ly == TILE) * (TILE - 1) * TILE1 + (lx - 1) * TILE1 + lz;
-  return 2 * TILE1 * TILE1 + 2 * (TILE - 1) * TILE1 + (lz == TILE) * (TILE - 1) * (TILE - 1) +
-         (lx - 1) * (TILE - 1) + (ly - 1);
+  // cells of the (TE+1)^3 block with a coordinate in {0, TE}
+  constexpr int E = TE, E1 = TE + 1;
+  if (lx == 0 || lx == E) return (lx == E) * E1 * E1 + ly * E1 + lz;
+  if (ly == 0 || ly == E) return 2 * E1 * E1 + (ly == E) * (E - 1) * E1 + (lx - 1) * E1 + lz;
+  return 2 * E1 * E1 + 2 * (E - 1) * E1 + (lz == E) * (E - 1) * (E - 1) + (lx - 1) * (E - 1) + (ly - 1);
 }
 
+template <int TE = 16>
 __device__ __forceinline__ void shell_decode(int s, int* l) {
-  if (s < 2 * TILE1 * TILE1) {
-    l[0] = (s >= TILE1 * TILE1) ? TILE : 0;
-    s %= TILE1 * TILE1;
-    l[1] = s / TILE1;
-    l[2] = s % TILE1;
+  constexpr int E = TE, E1 = TE + 1;
+  if (s < 2 * E1 * E1) {
+    l[0] = (s >= E1 * E1) ? E : 0;
+    s %= E1 * E1;
+    l[1] = s / E1;
+    l[2] = s % E1;
     return;
   }
-  s -= 2 * TILE1 * TILE1;
-  if (s < 2 * (TILE - 1) * TILE1) {
-    l[1] = (s >= (TILE - 1) * TILE1) ? TILE : 0;
-    s %= (TILE - 1) * TILE1;
-    l[0] = 1 + s / TILE1;
-    l[2] = s % TILE1;
+  s -= 2 * E1 * E1;
+  if (s < 2 * (E - 1) * E1) {
+    l[1] = (s >= (E - 1) * E1) ? E : 0;
+    s %= (E - 1) * E1;
+    l[0] = 1 + s / E1;
+    l[2] = s % E1;
     return;
   }
-  s -= 2 * (TILE - 1) * TILE1;
-  l[2] = (s >= (TILE - 1) * (TILE - 1)) ? TILE : 0;
-  s %= (TILE - 1) * (TILE - 1);
-  l[0] = 1 + s / (TILE - 1);
-  l[1] = 1 + s % (TILE - 1);
+  s -= 2 * (E - 1) * E1;
+  l[2] = (s >= (E - 1) * (E - 1)) ? E : 0;
+  s %= (E - 1) * (E - 1);
+  l[0] = 1 + s / (E - 1);
+  l[1] = 1 + s % (E - 1);
 }
 
 // Deposit one warp's particles.  When the warp holds long runs of the same
@@ -314,8 +333,9 @@ __device__ __forceinline__ void shell_decode(int s, int* l) {
 // weights of <= 2^24 fits 32 bits) and its head lane adds the 8 corner sums;
 // otherwise every lane adds its own.
 constexpr int MERGE_RUNS = 8;
-template <class A>
+template <class A, int TE = 16>
 __device__ __forceinline__ void deposit_warp(const A& acc, bool active, const int* l, const float* t) {
+  constexpr int E = TE, E1 = TE + 1;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   uint32_t w[8];
@@ -325,15 +345,15 @@ __device__ __forceinline__ void deposit_warp(const A& acc, bool active, const in
     for (int c = 0; c < 8; ++c)
       w[c] = active ? __float2uint_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * W_ONE) : 0u;
   }
-  const int key = active ? (l[0] * TILE + l[1]) * TILE + l[2] : -1 - lane;
+  const int key = active ? (l[0] * E + l[1]) * E + l[2] : -1 - lane;
   const int prev = __shfl_up_sync(full, key, 1);
   const bool head = (lane == 0) || (prev != key);
   const unsigned heads = __ballot_sync(full, head);
-  const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
+  const int base = (l[0] * E1 + l[1]) * E1 + l[2];
   if (__popc(heads) > MERGE_RUNS) {
     if (active) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
+      for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * E1 * E1 + ((c >> 1) & 1) * E1 + (c & 1), w[c]);
     }
     return;
   }
@@ -346,7 +366,7 @@ __device__ __forceinline__ void deposit_warp(const A& acc, bool active, const in
   for (int c = 0; c < 8; ++c) w[c] = __reduce_add_sync(run, w[c]);
   if (active && head) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1), w[c]);
+    for (int c = 0; c < 8; ++c) acc.add(base + (c >> 2) * E1 * E1 + ((c >> 1) & 1) * E1 + (c & 1), w[c]);
   }
 }
 
@@ -365,6 +385,7 @@ __device__ __forceinline__ T ld_part(const T* p) {
 
 // Local cell (relative to tile origin o) and fraction of particle i at
 // displacement d.
+template <int TE = 16>
 __device__ __forceinline__ bool local_cell(const float* d, uint32_t i, const Geom& g, const int* o, int* l,
                                            float* t) {
   int q[3], c[3];
@@ -373,7 +394,7 @@ __device__ __forceinline__ bool local_cell(const float* d, uint32_t i, const Geo
   for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], g.nc, &c[a], &t[a]);
   for (int a = 0; a < 3; ++a) {
     l[a] = c[a] - o[a];
-    if (l[a] < 0 || l[a] >= TILE) {   // cannot happen for a consistent key; guard anyway
+    if (l[a] < 0 || l[a] >= TE) {     // cannot happen for a consistent key; guard anyway
       ok = false;
       l[a] = 0;
     }
@@ -381,32 +402,33 @@ __device__ __forceinline__ bool local_cell(const float* d, uint32_t i, const Geo
   return ok;
 }
 
-template <bool COH>
+template <bool COH, int TE = 16>
 __device__ __forceinline__ bool particle_local(const float* __restrict__ dx, size_t N, uint32_t i,
                                                const Geom& g, const int* o, int* l, float* t) {
   float d[3];   // the three gathers are issued back to back
 #pragma unroll
   for (int a = 0; a < 3; ++a) d[a] = ld_part<COH>(dx + a * N + i);
-  return local_cell(d, i, g, o, l, t);
+  return local_cell<TE>(d, i, g, o, l, t);
 }
 
-// Write the tile's interior cells (final) and its 17^3 shell (partials).
-template <class A>
+// Write the tile's interior cells (final) and its (TE+1)^3 shell (partials).
+template <class A, int TE = 16>
 __device__ __forceinline__ void paint_writeout(const A& acc, const int* o, int tile, const Geom& g,
                                                float* __restrict__ rho, unsigned long long* __restrict__ halo) {
+  constexpr int E = TE, E1 = TE + 1;
   const int nc = g.nc;
-  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
-    const int lx = 1 + k / ((TILE - 1) * (TILE - 1));
-    const int ly = 1 + (k / (TILE - 1)) % (TILE - 1);
-    const int lz = 1 + k % (TILE - 1);
+  for (int k = threadIdx.x; k < (E - 1) * (E - 1) * (E - 1); k += blockDim.x) {
+    const int lx = 1 + k / ((E - 1) * (E - 1));
+    const int ly = 1 + (k / (E - 1)) % (E - 1);
+    const int lz = 1 + k % (E - 1);
     rho[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
-        from_fix(acc.get((lx * TILE1 + ly) * TILE1 + lz), g.mass);
+        from_fix(acc.get((lx * E1 + ly) * E1 + lz), g.mass);
   }
-  unsigned long long* hb = halo + (size_t)tile * SHELL;
-  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
+  unsigned long long* hb = halo + (size_t)tile * TileC<TE>::SHELL;
+  for (int s = threadIdx.x; s < TileC<TE>::SHELL; s += blockDim.x) {
     int l[3];
-    shell_decode(s, l);
-    hb[s] = acc.get((l[0] * TILE1 + l[1]) * TILE1 + l[2]);
+    shell_decode<TE>(s, l);
+    hb[s] = acc.get((l[0] * E1 + l[1]) * E1 + l[2]);
   }
 }
 
@@ -416,20 +438,21 @@ __device__ __forceinline__ void paint_writeout(const uint32_t* lo, const uint32_
   paint_writeout(Acc32{const_cast<uint32_t*>(lo), const_cast<uint32_t*>(hi)}, o, tile, g, rho, halo);
 }
 
-// Hot-path paint: one CTA per tile, particles in bucket order.
-template <bool COH, class A>
+// Hot-path paint: one CTA per tile of edge TE, particles in bucket order.
+template <bool COH, class A, int TE = 16>
 __device__ __forceinline__ void body_paint_bucket_acc(const float* __restrict__ dx, size_t N,
                                                       const uint32_t* __restrict__ items,
                                                       const uint32_t* __restrict__ tile_start, Geom g,
                                                       float* __restrict__ rho, unsigned long long* __restrict__ halo,
                                                       int* __restrict__ err, const A& acc, int bx,
                                                       const uint16_t* __restrict__ cells = nullptr) {
-  const int nt = g.nt;
+  using C = TileC<TE>;
+  const int nt = g.nc / TE;
   const int tile = bx;
-  const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
+  const int o[3] = {(tile / (nt * nt)) * TE, ((tile / nt) % nt) * TE, (tile % nt) * TE};
   const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
   const int n = (int)(s1 - s0);
-  for (int k = threadIdx.x; k < ACC; k += blockDim.x) acc.zero(k);
+  for (int k = threadIdx.x; k < C::ACC; k += blockDim.x) acc.zero(k);
   __syncthreads();
   bool bad = false;
   const int nw = (n + 31) & ~31;
@@ -440,25 +463,25 @@ __device__ __forceinline__ void body_paint_bucket_acc(const float* __restrict__ 
     if (active) {
       const uint32_t i = ld_part<COH>(items + s0 + k);
       if (cells) {
-        // in-tile cell from the bucketing (the key's low 12 bits), fraction from dx
+        // in-tile cell from the bucketing (the key's low 3 log2 TE bits), fraction from dx
         const uint32_t lc = ld_part<COH>(cells + s0 + k);
-        l[0] = (int)(lc >> 8);
-        l[1] = (int)(lc >> 4) & (TILE - 1);
-        l[2] = (int)lc & (TILE - 1);
+        l[0] = (int)(lc >> (2 * C::LG));
+        l[1] = (int)(lc >> C::LG) & (TE - 1);
+        l[2] = (int)lc & (TE - 1);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const float d = ld_part<COH>(dx + a * N + i);
           t[a] = d - floorf(d);
         }
       } else {
-        bad |= !particle_local<COH>(dx, N, i, g, o, l, t);
+        bad |= !particle_local<COH, TE>(dx, N, i, g, o, l, t);
       }
     }
-    deposit_warp(acc, active, l, t);
+    deposit_warp<A, TE>(acc, active, l, t);
   }
   if (bad) atomicOr(err, ERR_RANGE);
   __syncthreads();
-  paint_writeout(acc, o, tile, g, rho, halo);
+  paint_writeout<A, TE>(acc, o, tile, g, rho, halo);
 }
 
 template <bool COH = false>
@@ -471,31 +494,36 @@ __device__ __forceinline__ void body_paint_bucket(const float* __restrict__ dx, 
 }
 
 // Lower-face cells of every tile: sum the shell partials of the up to 8
-// tiles whose 17^3 blocks cover the cell.  One thread per face cell.
+// tiles whose (TE+1)^3 blocks cover the cell.  One thread per face cell.
 // nb: 8 words of shared memory.
 // In-tile coordinates of lower-face cell k < NFACE: the x = 0 face, then
 // y = 0 (x >= 1), then z = 0 (x, y >= 1).
+template <int TE = 16>
 __device__ __forceinline__ void face_cell(int k, int* l) {
-  if (k < TILE * TILE) {
+  constexpr int E = TE, LG = TileC<TE>::LG;
+  if (k < E * E) {
     l[0] = 0;
-    l[1] = k >> 4;
-    l[2] = k & 15;
-  } else if (k < TILE * TILE + (TILE - 1) * TILE) {
-    const int r = k - TILE * TILE;
-    l[0] = 1 + (r >> 4);
+    l[1] = k >> LG;
+    l[2] = k & (E - 1);
+  } else if (k < E * E + (E - 1) * E) {
+    const int r = k - E * E;
+    l[0] = 1 + (r >> LG);
     l[1] = 0;
-    l[2] = r & 15;
+    l[2] = r & (E - 1);
   } else {
-    const int r = k - TILE * TILE - (TILE - 1) * TILE;
-    l[0] = 1 + r / (TILE - 1);
-    l[1] = 1 + r % (TILE - 1);
+    const int r = k - E * E - (E - 1) * E;
+    l[0] = 1 + r / (E - 1);
+    l[1] = 1 + r % (E - 1);
     l[2] = 0;
   }
 }
 
+template <int TE = 16>
 __device__ __forceinline__ void body_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
                                                 float* __restrict__ rho, uint32_t* nb, int bx) {
-  const int nt = g.nt, nc = g.nc;
+  using C = TileC<TE>;
+  constexpr int E = TE;
+  const int nc = g.nc, nt = nc / TE;
   const int tile = bx;
   const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
   if (threadIdx.x < 8) {
@@ -504,18 +532,17 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
     nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < NFACE; k += blockDim.x) {
+  for (int k = threadIdx.x; k < C::NFACE; k += blockDim.x) {
     int l[3];
-    face_cell(k, l);
+    face_cell<TE>(k, l);
     unsigned long long sum = 0;
   #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
       if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
-      sum += __ldcg(halo + (size_t)nb[b] * SHELL + shell_index(l[0] + TILE * bx, l[1] + TILE * by, l[2] + TILE * bz));
+      sum += __ldcg(halo + (size_t)nb[b] * C::SHELL + shell_index<TE>(l[0] + E * bx, l[1] + E * by, l[2] + E * bz));
     }
-    rho[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
-        from_fix(sum, g.mass);
+    rho[((size_t)(tc[0] * E + l[0]) * nc + tc[1] * E + l[1]) * nc + tc[2] * E + l[2]] = from_fix(sum, g.mass);
   }
 }
 
@@ -579,7 +606,7 @@ __device__ __forceinline__ void corner_force(const float* __restrict__ F, size_t
   }
 }
 
-template <bool KDK, bool F4, bool COH = false>
+template <bool KDK, bool F4, bool COH = false, int TE = 16>
 __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __restrict__ p,
                                                  const float* __restrict__ F, Geom g, size_t N, size_t M,
                                                  const double* __restrict__ fac, int ik1, int ik2, int idr,
@@ -656,9 +683,9 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
         if (keys) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-          const uint32_t key = tile_key(c, g.nt);
+          const uint32_t key = tile_key<TE>(c, g.nc / TE);
           keys[i] = key;
-          tile = key >> 12;
+          tile = key >> (3 * TileC<TE>::LG);
         }
       }
       if (!ok) atomicOr(err, ERR_NAN);
@@ -667,5 +694,115 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
   }
 }
 
+
+// ---------------------------------------------------------------- readout over Lagrangian bricks
+// Readout + kick + drift + next key over compact Lagrangian bricks.  A CTA
+// of KB_THREADS takes a brick of X x Y x Z lattice particles (x slowest)
+// and walks it IPX iterations per x plane, each warp a 32-particle z
+// segment: the force corners its particles gather lie in two x planes of
+// about (Y + 1) x (Z + 1) cells at a time, a window that stays in L1 (a
+// 16-byte float4 per cell) while the CTA marches through the brick, so each
+// force cell is fetched from L2 about once per brick rather than once per z
+// line.  The next iteration's dx and p are fetched (streamed, evict-first)
+// while the current one gathers.  Arithmetic and outputs are those of
+// body_readout<true, true>.  The force mesh is read through the read-only
+// path: it must not be written earlier in the same launch.
+constexpr int KB_THREADS = 256;
+
+template <int Z_, int IPX_, int X_>
+struct BrickShape {
+  static constexpr int Z = Z_;                          // z extent: Z / 32 warps per row
+  static constexpr int IPX = IPX_;                      // iterations per x plane
+  static constexpr int X = X_;                          // x planes per brick
+  static constexpr int RPI = (KB_THREADS / 32) / (Z / 32);   // y rows per iteration
+  static constexpr int Y = RPI * IPX;
+  static constexpr int ITERS = X * IPX;
+  static_assert(Z % 32 == 0 && (KB_THREADS / 32) % (Z / 32) == 0, "brick z extent");
+  static __host__ __device__ bool fits(int np) { return np % Z == 0 && np % Y == 0 && np % X == 0; }
+  static __host__ __device__ int blocks(int np) { return (np / X) * (np / Y) * (np / Z); }
+};
+
+template <class BS>
+__device__ __forceinline__ uint32_t brick_particle(int it, int bx, int by, int bz, int np) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int z = bz * BS::Z + (w % (BS::Z / 32)) * 32 + lane;
+  const int y = by * BS::Y + (it % BS::IPX) * BS::RPI + w / (BS::Z / 32);
+  const int x = bx * BS::X + it / BS::IPX;
+  return ((uint32_t)x * np + y) * np + z;
+}
+
+template <class BS, int TE = 16>
+__device__ __forceinline__ void body_kdk_brick(float* __restrict__ dx, float* __restrict__ p,
+                                               const float4* __restrict__ F, const Geom& g, size_t N,
+                                               const double* __restrict__ fac, int ik1, int ik2, int idr,
+                                               uint32_t* __restrict__ keys, uint32_t* __restrict__ tile_count,
+                                               int* __restrict__ err, int blk) {
+  const int np = g.np, nc = g.nc;
+  const int nbz = np / BS::Z, nby = np / BS::Y;
+  const int bz = blk % nbz, by = (blk / nbz) % nby, bx = blk / (nbz * nby);
+  const float K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
+  const float D = idr >= 0 ? (float)fac[idr] : 0.f;
+  float dn[3], pn[3];
+  {
+    const uint32_t i = brick_particle<BS>(0, bx, by, bz, np);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dn[a] = __ldcs(dx + a * N + i);
+      pn[a] = __ldcs(p + a * N + i);
+    }
+  }
+#pragma unroll 1
+  for (int it = 0; it < BS::ITERS; ++it) {
+    const uint32_t i = brick_particle<BS>(it, bx, by, bz, np);
+    float d[3] = {dn[0], dn[1], dn[2]}, pp[3] = {pn[0], pn[1], pn[2]};
+    if (it + 1 < BS::ITERS) {
+      const uint32_t inext = brick_particle<BS>(it + 1, bx, by, bz, np);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dn[a] = __ldcs(dx + a * N + inext);
+        pn[a] = __ldcs(p + a * N + inext);
+      }
+    }
+    int q[3], c[3];
+    float t[3];
+    lattice_node(i, g, q);
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+    const int cx1 = (c[0] + 1 == nc) ? 0 : c[0] + 1;
+    const int cy1 = (c[1] + 1 == nc) ? 0 : c[1] + 1;
+    const int cz1 = (c[2] + 1 == nc) ? 0 : c[2] + 1;
+    const size_t rx[2] = {(size_t)c[0] * nc * nc, (size_t)cx1 * nc * nc};
+    const int ry[2] = {c[1] * nc, cy1 * nc};
+    const int rz[2] = {c[2], cz1};
+    const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+    float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const float4 v = __ldg(F + rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1]);
+      const float wt = wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1];
+      f[0] = fmaf(wt, v.x, f[0]);
+      f[1] = fmaf(wt, v.y, f[1]);
+      f[2] = fmaf(wt, v.z, f[2]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float pa = fmaf(K, f[a], pp[a]);
+      __stcs(p + a * N + i, pa);
+      d[a] = fmaf(D, pa, d[a]);
+      __stcs(dx + a * N + i, d[a]);
+    }
+    int tile = 0;
+    if (keys) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+      const uint32_t key = tile_key<TE>(c, g.nc / TE);
+      keys[i] = key;
+      tile = key >> (3 * TileC<TE>::LG);
+    }
+    if (!ok) atomicOr(err, ERR_NAN);
+    if (keys) warp_count(tile_count, tile, true);
+  }
+}
 
 }  // namespace fpm

@@ -3,10 +3,16 @@
 Per primitive: relative L2 <= 1e-5 (fixed positions, linear maps); reverse
 KDK and 2LPT <= 1e-4; the full gradient of chi^2 with respect to the white
 noise at 128^3 / 128^3, 400 Mpc/h, 5 steps: vector-norm relative error over
-32 random voxels <= 1e-3 against the oracle adjoint, and against central
-finite differences of the FP32 GPU forward (eps = 1e-3 and 3e-3), whose
-rounding noise is estimated from the spread of the two.
+32 random voxels <= 1e-3 against the oracle adjoint and against the FP64
+oracle's central finite differences at eps = 1e-4 (converged), <= 1e-2
+against those at eps = 1e-3 (which carry the CIC kinks crossed within the
+step); the FP32 GPU forward's own differences (all-voxel directional and
+per voxel) are printed with their noise and checked at their measured
+level.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +22,8 @@ from paper_2010_11847_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 COSMO = dict(inputs.COSMO_DEFAULT)
+FULL_EPS = (3e-4, 1e-3, 3e-3)
+VOXEL_FD_BOUND = 3e-2
 OM = COSMO["omega_m"]
 
 
@@ -147,13 +155,46 @@ def test_differentiable_config_gradient(torch_mod):
     assert vec < 1e-3
     assert rel_l2(g, g_ref.reshape(-1)) < 1e-3
 
-    # central finite differences of the FP32 GPU forward, voxel by voxel:
-    # chi^2 sums ~2e6 float32 residuals, so its rounding noise (~1e-3
-    # absolute) swamps 2 eps dchi2/dw at eps = 1e-3; larger eps shows the
-    # agreement (the loss is smooth on that scale)
+    # FP64 central differences of the oracle's forward (FP64 positions) at the
+    # same 32 voxels, written by tests/golden/make_fd_gradient_128.py: at
+    # eps = 1e-4 they have converged to the gradient (the chi^2 is piecewise
+    # smooth: a CIC weight's derivative jumps where a particle crosses a cell
+    # face); at eps = 1e-3 they still carry the kinks crossed within the
+    # step (the oracle's own FP64 adjoint is 3.9e-3 from them)
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fd_gradient_128.json")))
+    assert gold["voxels"] == [int(i) for i in idx]
+    assert gold["eps"] == 1e-3 and gold["eps_converged"] == 1e-4
+    fd3, fd4 = np.asarray(gold["fd"]), np.asarray(gold["fd_converged"])
+    vec3 = np.linalg.norm(ad - fd3) / np.linalg.norm(fd3)
+    vec4 = np.linalg.norm(ad - fd4) / np.linalg.norm(fd4)
+    print(f"adjoint vs FP64 central differences, 32 voxels: eps=1e-4 vector rel {vec4:.2e} "
+          f"(per-voxel max {np.max(np.abs(ad - fd4) / np.abs(fd4)):.2e}); eps=1e-3 vector rel {vec3:.2e}")
+    assert vec4 < 1e-3
+    assert vec3 < 1e-2
+
     def gpu_loss(wv):
         with torch.no_grad():
             return float(chi2_of_final_density(wv, tt, pl, stages))
+
+    # FP32 GPU forward, central directional derivative along a direction that
+    # spans every voxel (unit variance per voxel): its signal 2 eps g.u grows
+    # like sqrt(N) over a single voxel's; at small eps the FP32 rounding of
+    # the loss and at large eps the CIC kinks crossed by the moving particles
+    # bound the agreement (measured 1e-3..3e-3 at eps = 3e-4, 1e-2..2e-2 at 1e-3)
+    u = np.random.default_rng(7).standard_normal(w.size).astype(np.float32)
+    ut = torch.from_numpy(u).cuda().view(w.shape)
+    exact = float(g.astype(np.float64) @ u.astype(np.float64))
+    full = {}
+    for eps in FULL_EPS:
+        full[eps] = (gpu_loss(wt.detach() + eps * ut) - gpu_loss(wt.detach() - eps * ut)) / (2 * eps)
+        print(f"FP32 directional derivative over all voxels eps={eps:g}: rel error "
+              f"{abs(full[eps] - exact) / abs(exact):.2e}")
+    assert abs(full[3e-4] - exact) < 1e-2 * abs(exact)
+
+    # FP32 central differences voxel by voxel: the loss's FP32 rounding noise
+    # (printed, implied by |fd - ad| 2 eps) swamps 2 eps dchi2/dw at small
+    # eps, and at eps = 3e-2 the kinks crossed within the step dominate (the
+    # FP64 differences are 3.9e-3 off already at a 30x smaller step)
     fds = {}
     for eps in (1e-3, 3e-3, 3e-2):
         out = []
@@ -165,21 +206,9 @@ def test_differentiable_config_gradient(torch_mod):
         fds[eps] = np.array(out)
     for eps, fd in fds.items():
         print(f"FP32 central differences eps={eps:g}: vector rel error vs adjoint "
-              f"{np.linalg.norm(fd - ad) / np.linalg.norm(ad):.2e}")
-    # the FP32 differences converge toward the adjoint as eps grows (error ~
-    # rounding noise / eps: 0.28, 0.10, 0.01 at eps = 1e-3, 3e-3, 3e-2); the
-    # 1e-3 agreement is shown in FP64 by the oracle pins plus the comparison above
-    assert np.linalg.norm(fds[3e-2] - ad) / np.linalg.norm(ad) < 3e-2
-    # directional derivative along a random direction on the 32 voxels
-    u = np.zeros(w.size, dtype=np.float32)
-    u[idx] = np.random.default_rng(7).standard_normal(32).astype(np.float32)
-    ut = torch.from_numpy(u).cuda().view(w.shape)
-    dds = {}
-    for eps in (1e-3, 1e-2, 3e-2):
-        dds[eps] = (gpu_loss(wt.detach() + eps * ut) - gpu_loss(wt.detach() - eps * ut)) / (2 * eps)
-        print(f"FP32 directional derivative eps={eps:g}: rel error "
-              f"{abs(dds[eps] - float(ad @ u[idx])) / abs(float(ad @ u[idx])):.2e}")
-    assert abs(dds[3e-2] - float(ad @ u[idx])) < 3e-2 * abs(float(ad @ u[idx]))
+              f"{np.linalg.norm(fd - ad) / np.linalg.norm(ad):.2e}, implied loss noise "
+              f"{np.median(np.abs(fd - ad)) * 2 * eps:.2e}")
+    assert np.linalg.norm(fds[3e-2] - ad) / np.linalg.norm(ad) < VOXEL_FD_BOUND
 
 
 @pytest.mark.parametrize("np_,nc,reverse", [(32, 64, True), (32, 32, True), (48, 96, False)])
