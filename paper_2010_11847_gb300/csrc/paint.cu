@@ -425,6 +425,72 @@ __global__ void __launch_bounds__(256) k_gather_adj(const float* __restrict__ dx
   }
 }
 
+// The same transposed gather over the Lagrangian bricks of the fused
+// readout (KdkBrick): the mesh corners a CTA's particles touch stay in L1
+// while it marches through its brick.  Identical arithmetic per particle.
+template <bool F4>
+__global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __restrict__ dx, Geom g, size_t N,
+                                                                 size_t M, const float* __restrict__ g_rho,
+                                                                 const float* __restrict__ F,
+                                                                 const float* __restrict__ v,
+                                                                 float* __restrict__ g_dx, int accumulate) {
+  using BS = KdkBrick;
+  const int np = g.np, nc = g.nc;
+  const int nbz = np / BS::Z, nby = np / BS::Y;
+  const int blk = blockIdx.x;
+  const int bz = blk % nbz, by = (blk / nbz) % nby, bx = blk / (nbz * nby);
+  float dn[3], vn[3] = {0.f, 0.f, 0.f};
+  {
+    const uint32_t i = brick_particle<BS>(0, bx, by, bz, np);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dn[a] = __ldcs(dx + a * N + i);
+      if (v) vn[a] = __ldcs(v + a * N + i);
+    }
+  }
+#pragma unroll 1
+  for (int it = 0; it < BS::ITERS; ++it) {
+    const uint32_t i = brick_particle<BS>(it, bx, by, bz, np);
+    const float d[3] = {dn[0], dn[1], dn[2]}, vi[3] = {vn[0], vn[1], vn[2]};
+    if (it + 1 < BS::ITERS) {
+      const uint32_t inext = brick_particle<BS>(it + 1, bx, by, bz, np);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dn[a] = __ldcs(dx + a * N + inext);
+        if (v) vn[a] = __ldcs(v + a * N + inext);
+      }
+    }
+    int q[3], c[3];
+    float t[3];
+    lattice_node(i, g, q);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cic_cell(d[a], q[a], nc, &c[a], &t[a]);
+    const int c1[3] = {c[0] + 1 == nc ? 0 : c[0] + 1, c[1] + 1 == nc ? 0 : c[1] + 1, c[2] + 1 == nc ? 0 : c[2] + 1};
+    float gsum[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int bx_ = b >> 2, by_ = (b >> 1) & 1, bz_ = b & 1;
+      const size_t idx = ((size_t)(bx_ ? c1[0] : c[0]) * nc + (by_ ? c1[1] : c[1])) * nc + (bz_ ? c1[2] : c[2]);
+      float s = 0.f;
+      if (g_rho) s = g.mass * __ldg(g_rho + idx);
+      if (v) {
+        if (F4) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(F) + idx);
+          s = fmaf(vi[0], f.x, fmaf(vi[1], f.y, fmaf(vi[2], f.z, s)));
+        } else {
+          for (int a = 0; a < 3; ++a) s = fmaf(vi[a], __ldg(F + a * M + idx), s);
+        }
+      }
+      const float wx = bx_ ? t[0] : 1.f - t[0], wy = by_ ? t[1] : 1.f - t[1], wz = bz_ ? t[2] : 1.f - t[2];
+      gsum[0] = fmaf((bx_ ? 1.f : -1.f) * wy * wz, s, gsum[0]);
+      gsum[1] = fmaf((by_ ? 1.f : -1.f) * wx * wz, s, gsum[1]);
+      gsum[2] = fmaf((bz_ ? 1.f : -1.f) * wx * wy, s, gsum[2]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) __stcs(g_dx + a * N + i, accumulate ? __ldcs(g_dx + a * N + i) + gsum[a] : gsum[a]);
+  }
+}
+
 // max |v| over n values as the bit pattern of a non-negative float (the
 // integer order of such patterns is their numeric order): order-independent.
 __global__ void k_maxabs(const float* __restrict__ v, size_t n, unsigned* __restrict__ out) {
@@ -582,7 +648,14 @@ __global__ void __launch_bounds__(768) k_halo_vec(const unsigned long long* __re
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
                       const float* v, float* g_dx, bool accumulate, cudaStream_t s) {
   const int it = readout_iters(c.N);
-  if (f4)
+  if (KDK_BRICK && KdkBrick::fits(c.g.np)) {
+    if (f4)
+      k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx,
+                                                                              accumulate);
+    else
+      k_gather_adj_brick<false><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v,
+                                                                               g_dx, accumulate);
+  } else if (f4)
     k_gather_adj<true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate, it);
   else
     k_gather_adj<false><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate,
