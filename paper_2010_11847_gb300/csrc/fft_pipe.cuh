@@ -15,6 +15,8 @@
 //   X   x pass with the Green's function: L lines, all kx -> staged [kx][L]
 // The same buffer then holds the line-major exchange area (stride RL).
 #pragma once
+#include <cuda.h>
+#include "bulk.cuh"
 #include "fft_reg.cuh"
 
 namespace fpm {
@@ -48,11 +50,12 @@ struct PipeCfg {
   static constexpr int NH = N / 2 + 1;
   static constexpr int RL = N + 2;                  // line-major exchange (swizzled), 16-byte aligned
   static constexpr int RLX = N + N / 8 + (N == 128 ? 1 : 2);   // x pass exchange (padded)
-  static constexpr int BUF = L * RLX;               // float2 per stage buffer
+  static constexpr int BUF = (L * RLX + 15) & ~15;  // float2 per stage buffer (a multiple of 128 bytes)
   static constexpr size_t SMEM = (size_t)(N + 2 * BUF) * sizeof(float2);
   static constexpr int ZI_PER = (NH * L + THREADS - 1) / THREADS;
   static constexpr int ZI = N / (2 * L);            // z items per x plane
-  static_assert(L * N <= BUF && NH * 2 * L <= BUF && L * RL <= BUF, "stage buffer too small");
+  static_assert(L * N <= BUF && (NH + 1) * 2 * L <= BUF && L * RL <= BUF, "stage buffer too small");
+  static_assert((N * sizeof(float2)) % 128 == 0 && (BUF * sizeof(float2)) % 128 == 0, "buffers 128-byte aligned");
   static_assert(L % 2 == 0 && N % L == 0, "x items must be whole 16-byte chunks of one kz row");
 };
 
@@ -96,6 +99,72 @@ __device__ __forceinline__ void issue_x(const float2* spec, int gl0, float2* buf
     const int kx = c / CPK, j = c - kx * CPK;
     cp_async16(buf + kx * L + 2 * j, spec + kx * S + gl0 + 2 * j);
   }
+}
+
+// ---------------------------------------------------------------- staging by the tensor memory accelerator
+// The same stage-buffer layouts filled by one thread's bulk copies (TMA),
+// completing on the buffer's mbarrier: the z r2c rows and the y lines are
+// contiguous (1-D bulk copies); the z c2r strips ([kz][2L]) and the x lines
+// ([kx][L]) are boxes of 2-D tensor maps of the half spectrum.  Returns the
+// bytes the barrier must expect.
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* tm, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t tma_issue_zf(const float* rho, size_t r0, float2* buf, unsigned long long* bar,
+                                                 unsigned long long pol) {
+  using P = PipeCfg<N>;
+  constexpr uint32_t bytes = 2 * P::L * N * sizeof(float);
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s(buf, rho + r0 * N, bytes, bar, pol);
+  return bytes;
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t tma_issue_y(const float2* base, int l0, int nlines, float2* buf,
+                                                unsigned long long* bar, unsigned long long pol) {
+  using P = PipeCfg<N>;
+  const int nl = nlines - l0 < P::L ? nlines - l0 : P::L;
+  const uint32_t bytes = (uint32_t)nl * N * sizeof(float2);
+  mbar_expect_tx(bar, bytes);
+  for (int g = 0; g < nl; ++g) bulk_g2s(buf + g * P::RL, base + (size_t)(l0 + g) * N, N * sizeof(float2), bar, pol);
+  return bytes;
+}
+
+// z c2r strip of plane x, rows y0 .. y0 + 2L - 1, every kz: boxes of
+// ZiBox<N>::ROWS kz rows (a box of at most 256 rows, each box's destination
+// 128-byte aligned; rows past kz = N/2 land in the buffer's spare room and
+// are not used)
+template <int N>
+struct ZiBox {
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int ROWS = NH <= 256 ? NH : 86;
+  static constexpr int BOXES = (NH + ROWS - 1) / ROWS;
+};
+template <int N>
+__device__ __forceinline__ void tma_issue_zi(const CUtensorMap* tm, size_t r0, float2* buf, unsigned long long* bar) {
+  using P = PipeCfg<N>;
+  using Z = ZiBox<N>;
+  static_assert((Z::ROWS * 2 * P::L * sizeof(float2)) % 128 == 0 || Z::BOXES == 1, "box destinations 128-byte aligned");
+  static_assert(Z::BOXES * Z::ROWS * 2 * P::L <= P::BUF, "boxes fit the stage buffer");
+  const int x = (int)(r0 / N), y0 = (int)(r0 - (size_t)x * N);
+  mbar_expect_tx(bar, Z::BOXES * Z::ROWS * 4 * P::L * sizeof(float));
+#pragma unroll
+  for (int b = 0; b < Z::BOXES; ++b) tma_2d(buf + b * Z::ROWS * 2 * P::L, tm, 2 * y0, x * P::NH + b * Z::ROWS, bar);
+}
+
+// x pass: lines gl0 .. gl0 + L - 1 of every kx, two boxes of N/2 kx rows
+template <int N>
+__device__ __forceinline__ void tma_issue_x(const CUtensorMap* tm, int gl0, float2* buf, unsigned long long* bar) {
+  using P = PipeCfg<N, true>;
+  mbar_expect_tx(bar, N * 2 * P::L * sizeof(float));
+  tma_2d(buf, tm, 2 * gl0, 0, bar);
+  tma_2d(buf + (N / 2) * P::L, tm, 2 * gl0, N / 2, bar);
 }
 
 // ---------------------------------------------------------------- transforms from the stage buffer

@@ -27,9 +27,16 @@
 #include "internal.h"
 #include "fft_pipe.cuh"
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <vector>
+
 namespace fpm {
 
 struct PipeArgs {
+  CUtensorMap tm_zi;    // the half spectrum as [x * NH + kz][2N floats] rows (z c2r strips)
+  CUtensorMap tm_x;     // the half spectrum as [kx][2 NH N floats] rows (x lines)
   const float* rho;     // forward: real mesh
   float2* spec;         // half spectrum [x][kz][y]
   float* phi;           // inverse: real potential
@@ -137,6 +144,20 @@ __device__ __forceinline__ void pipe_issue(const PipeArgs& a, const PipeSched<N,
 }
 
 template <int N, int KIND>
+__device__ __forceinline__ void pipe_issue_tma(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item, float2* buf,
+                                               unsigned long long* bar, unsigned long long pol) {
+  using P = PipeCfg<N, KIND == PK_X>;
+  int ph, s, j;
+  sc.decode(item, &ph, &s, &j);
+  float2* slab = a.spec + (size_t)s * sc.S * P::NH * N;
+  const bool zitem = (KIND == PK_FWD && ph == 0) || (KIND == PK_INV && ph == 1);
+  if (KIND == PK_X) tma_issue_x<N>(&a.tm_x, j * P::L, buf, bar);
+  else if (zitem && KIND == PK_FWD) tma_issue_zf<N>(a.rho, (size_t)(s * sc.S * P::ZI + j) * 2 * P::L, buf, bar, pol);
+  else if (zitem) tma_issue_zi<N>(&a.tm_zi, (size_t)(s * sc.S * P::ZI + j) * 2 * P::L, buf, bar);
+  else tma_issue_y<N>(slab, j * P::L, sc.S * P::NH, buf, bar, pol);
+}
+
+template <int N, int KIND>
 __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<N, KIND>& sc, int item,
                                              float2* buf, const float2* tw) {
   using P = PipeCfg<N, KIND == PK_X>;
@@ -162,13 +183,22 @@ __device__ __forceinline__ void pipe_compute(const PipeArgs& a, const PipeSched<
   }
 }
 
-template <int N, int KIND>
+// TMA: the stage buffers are filled by one thread's bulk / tensor copies
+// completing on a per-buffer mbarrier (item i: buffer i & 1, its (i >> 1)-th
+// fill, phase parity (i >> 1) & 1); else by every thread's cp.async.  Every
+// thread fences its generic accesses of a buffer before the block barrier
+// that hands it back to the copy engine.
+template <int N, int KIND, bool TMA>
 __global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS,
                                   KIND == PK_INV ? PipeCfg<N>::MINB_INV : PipeCfg<N, KIND == PK_X>::MINB)
-    k_pipe(PipeArgs a) {
+    k_pipe(const __grid_constant__ PipeArgs a) {
   using P = PipeCfg<N, KIND == PK_X>;
-  extern __shared__ __align__(16) float2 smem[];
+  extern __shared__ __align__(128) float2 smem_raw[];
   __shared__ int s_item, s_ready;
+  __shared__ __align__(8) unsigned long long bars[2];
+  // tensor copies need 128-byte aligned destinations: align the base (the
+  // launch adds 128 bytes), the buffers then start at multiples of 128 bytes
+  float2* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u) / sizeof(float2);
   float2* tw = smem;
   float2* bufs = smem + N;
   for (int i = threadIdx.x; i < N; i += P::THREADS) tw[i] = a.tw[i];
@@ -179,6 +209,22 @@ __global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS,
     sc.decode(item, &ph, &s, &j);
     return ph == 1 ? s : -1;
   };
+  unsigned long long pol = 0;
+  if (TMA && threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init_fence();
+    pol = l2_evict_first();
+  }
+  auto issue = [&](int item, int i) {      // stage `item` as the block's i-th item
+    float2* dst = bufs + (i & 1) * P::BUF;
+    if (TMA) {
+      if (threadIdx.x == 0) pipe_issue_tma<N, KIND>(a, sc, item, dst, &bars[i & 1], pol);
+    } else {
+      pipe_issue<N, KIND>(a, sc, item, dst);
+    }
+  };
+  bool live = true;
   __syncthreads();
   if (threadIdx.x == 0) {
     const int it = (int)atomicAdd(a.ctr, 1u);
@@ -187,11 +233,10 @@ __global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS,
   }
   __syncthreads();
   int cur = s_item;
-  if (cur < sc.total) pipe_issue<N, KIND>(a, sc, cur, bufs);
-  cp_async_commit();
+  if (cur < sc.total) issue(cur, 0);
+  if (!TMA) cp_async_commit();
   for (int i = 0; cur < sc.total; ++i) {
     float2* b = bufs + (i & 1) * P::BUF;
-    float2* bn = bufs + ((i + 1) & 1) * P::BUF;
     __syncthreads();                       // bn (item i-1's buffer) and s_item are free
     if (threadIdx.x == 0) {
       const int it = (int)atomicAdd(a.ctr, 1u);
@@ -202,20 +247,25 @@ __global__ void __launch_bounds__(PipeCfg<N, KIND == PK_X>::THREADS,
     __syncthreads();
     const int nxt = s_item;
     const bool ready = s_ready != 0;
-    if (nxt < sc.total && ready) pipe_issue<N, KIND>(a, sc, nxt, bn);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
+    if (nxt < sc.total && ready) issue(nxt, i + 1);
+    if (TMA) {   // after a wait that ran out, later ones keep waiting, but briefly
+      live = mbar_wait(&bars[i & 1], (uint32_t)((i >> 1) & 1), live ? a.wait_ns : 1000000ll, a.err) && live;
+    } else {
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();
+    }
     pipe_compute<N, KIND>(a, sc, cur, b, tw);
+    if (TMA) fence_proxy_async();          // this buffer goes back to the copy engine
     if (nxt < sc.total && !ready) {        // wait only while holding no unfinished item
       if (threadIdx.x == 0) wait_count(a.ctr + 1 + slab_of(nxt), sc.nA, a.wait_ns, a.err);
       __syncthreads();
-      pipe_issue<N, KIND>(a, sc, nxt, bn);
-      cp_async_commit();
+      issue(nxt, i + 1);
+      if (!TMA) cp_async_commit();
     }
     cur = nxt;
   }
-  cp_async_wait0();
+  if (!TMA) cp_async_wait0();
 }
 
 // ---------------------------------------------------------------- host side
@@ -236,21 +286,94 @@ int fft_slab_planes(int n) {
 
 bool fft_has_potential(int n) { return is_pow2_size(n); }
 
+// Tensor maps of a half spectrum at `spec` (N^3 mesh) for the z c2r strips
+// and the x lines, encoded once per buffer through the driver's
+// cuTensorMapEncodeTiled (reached through the runtime, no driver library
+// link) and cached.
+namespace {
+struct MapEntry {
+  const void* spec;
+  int n;
+  CUtensorMap zi, x;
+};
+std::mutex g_map_mu;
+std::vector<MapEntry> g_maps;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+bool g_encode_tried = false;
+
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+               uint32_t box_inner, uint32_t box_rows) {
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N>
+bool spectrum_maps(const float2* spec, CUtensorMap* zi, CUtensorMap* x) {
+  std::lock_guard<std::mutex> lock(g_map_mu);
+  if (!g_encode_tried) {
+    g_encode_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  }
+  if (!g_encode) return false;
+  for (const MapEntry& e : g_maps)
+    if (e.spec == spec && e.n == N) {
+      *zi = e.zi;
+      *x = e.x;
+      return true;
+    }
+  using PS = PipeCfg<N>;
+  using PX = PipeCfg<N, true>;
+  constexpr int NH = N / 2 + 1;
+  MapEntry e;
+  e.spec = spec;
+  e.n = N;
+  // z c2r: rows x * NH + kz of N complex (2N floats); box 2L complex x ZiBox rows
+  // x pass: rows kx of NH N complex; box L complex x N/2 rows
+  if (!encode_2d(&e.zi, spec, 2ull * N, (uint64_t)N * NH, 2ull * N * sizeof(float), 4 * PS::L, ZiBox<N>::ROWS) ||
+      !encode_2d(&e.x, spec, 2ull * NH * N, (uint64_t)N, 2ull * NH * N * sizeof(float), 2 * PX::L, N / 2))
+    return false;
+  if (g_maps.size() > 64) g_maps.clear();
+  g_maps.push_back(e);
+  *zi = e.zi;
+  *x = e.x;
+  return true;
+}
+}  // namespace
+
+// Stage the pencils with the tensor memory accelerator where the buffers
+// allow it (16-byte aligned mesh and spectrum, tensor maps available), else
+// with cp.async.
+constexpr bool PIPE_TMA = true;
+
 template <int N, int KIND>
 static int pipe_launch(const FftTables& t, const float* rho, float2* spec, float* phi, float coef, unsigned* ctr,
                        int* err, cudaStream_t s) {
   using P = PipeCfg<N, KIND == PK_X>;
-  static int grid = 0;                      // blocks that fit the device at once (persistent)
-  FPM_TRY(smem_attr(k_pipe<N, KIND>, P::SMEM));
-  if (grid == 0) {
+  PipeArgs a;
+  bool tma = PIPE_TMA && (uintptr_t)spec % 16 == 0 && (KIND != PK_FWD || (uintptr_t)rho % 16 == 0) &&
+             spectrum_maps<N>(spec, &a.tm_zi, &a.tm_x);
+  auto kern = tma ? k_pipe<N, KIND, true> : k_pipe<N, KIND, false>;
+  static int grid[2] = {0, 0};              // blocks that fit the device at once (persistent)
+  constexpr size_t smem = P::SMEM + 128;    // + the alignment pad of the stage buffers
+  FPM_TRY(smem_attr(kern, smem));
+  if (grid[tma] == 0) {
     int dev = 0, nsm = 0, per = 0;
     FPM_CUDA_TRY(cudaGetDevice(&dev));
     FPM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe<N, KIND>, P::THREADS, P::SMEM));
+    FPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, P::THREADS, smem));
     if (per < 1) return FPM_ECUDA;
-    grid = nsm * per;
+    grid[tma] = nsm * per;
   }
-  PipeArgs a;
   a.rho = rho;
   a.spec = spec;
   a.phi = phi;
@@ -264,12 +387,12 @@ static int pipe_launch(const FftTables& t, const float* rho, float2* spec, float
     // lag: about three grids' worth of items between a slab's two phases
     const int ns = N / a.S, ny = (a.S * P::NH + P::L - 1) / P::L, nz = a.S * P::ZI;
     int D = 1;
-    while (D < ns && D * (ny + nz) < 3 * grid) ++D;
+    while (D < ns && D * (ny + nz) < 3 * grid[tma]) ++D;
     a.D = D;
   }
   a.wait_ns = 4000000000ll;
   FPM_CUDA_TRY(cudaMemsetAsync(ctr, 0, (size_t)(1 + N / a.S) * sizeof(unsigned), s));
-  k_pipe<N, KIND><<<grid, P::THREADS, P::SMEM, s>>>(a);
+  kern<<<grid[tma], P::THREADS, smem, s>>>(a);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
