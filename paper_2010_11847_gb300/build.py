@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfpm.so")
-SOURCES = ["api.cu", "cosmo.cu", "fft.cu", "ic.cu", "paint.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "fft_slab.cu",
+SOURCES = ["api.cu", "cosmo.cu", "fft.cu", "ic.cu", "paint.cu", "readout.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "fft_slab.cu",
            "pyramid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

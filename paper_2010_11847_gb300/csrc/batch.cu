@@ -19,6 +19,7 @@
 #include "fft_passes.cuh"
 #include "fft_reg.cuh"
 #include "paint_dev.cuh"
+#include "readout_dev.cuh"
 
 #include <algorithm>
 #include <vector>

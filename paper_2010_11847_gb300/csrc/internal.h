@@ -108,6 +108,10 @@ int launch_halo(const PaintCtx& c, float* rho, cudaStream_t s);
 int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_out, cudaStream_t s);
 int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
                int ik2, int idr, bool emit_keys, cudaStream_t s);
+// readout.cu: the brick traversal of the fused readout (interleaved float4
+// force, lattice divisible by the brick); keys == nullptr emits no keys.
+int launch_kdk_brick(const PaintCtx& c, float* dx, float* p, const float4* F, const double* fac, int ik1,
+                     int ik2, int idr, uint32_t* keys, cudaStream_t s);
 
 // paint.cu: adjoints at fixed positions
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,

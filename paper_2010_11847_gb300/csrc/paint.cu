@@ -25,6 +25,7 @@
 // the last of the (up to 8) blocks whose shells cover a tile's lower faces
 // sums them (a separate face-sum kernel where no face counters are kept).
 #include "paint_dev.cuh"
+#include "readout_dev.cuh"
 
 namespace fpm {
 
@@ -97,18 +98,6 @@ __global__ void __launch_bounds__(256) k_readout(float* __restrict__ dx, float* 
                                                  uint32_t* __restrict__ tile_count, int* __restrict__ err,
                                                  int iters) {
   body_readout<KDK, F4>(dx, p, F, g, N, M, fac, ik1, ik2, idr, f_out, keys, tile_count, err, iters, blockIdx.x);
-}
-
-// Readout + kick + drift + next key over compact Lagrangian bricks
-// (body_kdk_brick): 4 x 16 x 64 particles per CTA, x slowest.
-using KdkBrick = BrickShape<64, 4, 4>;
-
-__global__ void __launch_bounds__(KB_THREADS) k_kdk_brick(float* __restrict__ dx, float* __restrict__ p,
-                                                          const float4* __restrict__ F, Geom g, size_t N,
-                                                          const double* __restrict__ fac, int ik1, int ik2, int idr,
-                                                          uint32_t* __restrict__ keys,
-                                                          uint32_t* __restrict__ tile_count, int* __restrict__ err) {
-  body_kdk_brick<KdkBrick>(dx, p, F, g, N, fac, ik1, ik2, idr, keys, tile_count, err, blockIdx.x);
 }
 
 // Paint with the permutation output: counting sort of the tile's bucket by
@@ -341,10 +330,9 @@ int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, 
   if (emit_keys) FPM_CUDA_TRY(cudaMemsetAsync(c.tile_count, 0, sizeof(uint32_t) * c.ntiles, s));
   const int it = readout_iters(c.N);
   uint32_t* keys = emit_keys ? c.keys : nullptr;
-  if (f4 && KDK_BRICK && KdkBrick::fits(c.g.np)) {
-    k_kdk_brick<<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, p, reinterpret_cast<const float4*>(F), c.g, c.N, fac, ik1, ik2, idr,
-                                          keys, c.tile_count, c.err);
-  } else if (f4)
+  if (f4 && KDK_BRICK && KdkBrick::fits(c.g.np))
+    return launch_kdk_brick(c, dx, p, reinterpret_cast<const float4*>(F), fac, ik1, ik2, idr, keys, s);
+  if (f4)
     k_readout<true, true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr,
                                                                  nullptr, keys, c.tile_count, c.err, it);
   else

@@ -1,7 +1,9 @@
 // paint_dev.cuh -- device bodies of the cell keys, tile sort, deterministic
 // CIC paint and fused readout-kick-drift (internal).  Each body takes its
 // block index (and any shared memory) explicitly, so that the same code runs
-// as its own kernel or as a phase of the batched persistent kernel.
+// as its own kernel or as a phase of the batched persistent kernel.  The
+// cell and key helpers are in cells.cuh, the brick traversal of the fused
+// readout in readout_dev.cuh.
 //
 // Sort.  The mesh is cut into 16^3-cell tiles.  Each particle's tile-major
 // cell key is computed from its float32 displacement (cell = wrap(q +
@@ -27,6 +29,7 @@
 // the last of the (up to 8) blocks whose shells cover a tile's lower faces
 // sums them (a separate face-sum kernel where no face counters are kept).
 #pragma once
+#include "cells.cuh"
 #include "internal.h"
 
 namespace fpm {
@@ -40,70 +43,7 @@ constexpr float W_ONE = 16777216.0f;              // 2^24: fixed-point unit of a
 constexpr float W_INV = 5.9604644775390625e-08f;  // 2^-24
 constexpr int NFACE = TILE * TILE + (TILE - 1) * TILE + (TILE - 1) * (TILE - 1);   // 721 lower-face cells
 
-// Geometry of a paint tile of edge TE (16: the cell key's tiles; 8: the
-// batched step may bucket and paint small meshes by 8^3 tiles).
-template <int TE>
-struct TileC {
-  static_assert(TE == 8 || TE == 16, "paint tile edge");
-  static constexpr int E = TE, E1 = TE + 1, E3 = TE * TE * TE, LG = TE == 8 ? 3 : 4;
-  static constexpr int ACC = E1 * E1 * E1;                                        // accumulator cells
-  static constexpr int SHELL = 2 * E1 * E1 + 2 * (E - 1) * E1 + 2 * (E - 1) * (E - 1);   // its shell
-  static constexpr int NFACE = E * E + (E - 1) * E + (E - 1) * (E - 1);            // lower-face cells
-};
 static_assert(TileC<16>::ACC == ACC && TileC<16>::SHELL == SHELL && TileC<16>::NFACE == NFACE, "16^3 tiles");
-
-// Wrap c into [0, n) for |c| < 2^31 - n (one correction in the common case).
-__device__ __forceinline__ int wrapi(int c, int n) {
-  if (c < 0) c += n;
-  if (c >= n) c -= n;
-  if ((unsigned)c >= (unsigned)n) {
-    c %= n;
-    if (c < 0) c += n;
-  }
-  return c;
-}
-
-__device__ __forceinline__ void lattice_node(uint32_t i, const Geom& g, int* q) {
-  const uint32_t ix = fdiv(i, g.div_np2);
-  const uint32_t rem = i - ix * g.div_np2.d;
-  const uint32_t iy = fdiv(rem, g.div_np);
-  const uint32_t iz = rem - iy * g.div_np.d;
-  q[0] = ix * g.ratio;
-  q[1] = iy * g.ratio;
-  q[2] = iz * g.ratio;
-}
-
-// Base cell and fraction from a float32 displacement.  Returns false (and
-// the cell 0) for a non-finite or absurdly large displacement.
-__device__ __forceinline__ bool cic_cell(float d, int q, int nc, int* c, float* t) {
-  if (!(fabsf(d) < 1.0e7f)) {
-    *c = 0;
-    *t = 0.f;
-    return false;
-  }
-  const float fl = floorf(d);
-  *c = wrapi(q + (int)fl, nc);
-  *t = d - fl;
-  return true;
-}
-
-// Tile-major key of cell c with TE^3 tiles, nt = nc / TE tiles per side.
-template <int TE = 16>
-__device__ __forceinline__ uint32_t tile_key(const int* c, int nt) {
-  using C = TileC<TE>;
-  const uint32_t tile = ((uint32_t)(c[0] >> C::LG) * nt + (c[1] >> C::LG)) * nt + (c[2] >> C::LG);
-  const uint32_t local = ((c[0] & (TE - 1)) * TE + (c[1] & (TE - 1))) * TE + (c[2] & (TE - 1));
-  return tile * C::E3 + local;
-}
-
-// Warp-aggregated increment of counter[bucket] for every active lane.
-__device__ __forceinline__ void warp_count(uint32_t* counter, int bucket, bool active) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int key = active ? bucket : -1 - lane;
-  const unsigned grp = __match_any_sync(full, key);
-  if (active && lane == __ffs(grp) - 1) atomicAdd(counter + bucket, (uint32_t)__popc(grp));
-}
 
 // ---------------------------------------------------------------- keys + tile histogram
 template <int TE = 16>
@@ -694,115 +634,5 @@ __device__ __forceinline__ void body_readout(float* __restrict__ dx, float* __re
   }
 }
 
-
-// ---------------------------------------------------------------- readout over Lagrangian bricks
-// Readout + kick + drift + next key over compact Lagrangian bricks.  A CTA
-// of KB_THREADS takes a brick of X x Y x Z lattice particles (x slowest)
-// and walks it IPX iterations per x plane, each warp a 32-particle z
-// segment: the force corners its particles gather lie in two x planes of
-// about (Y + 1) x (Z + 1) cells at a time, a window that stays in L1 (a
-// 16-byte float4 per cell) while the CTA marches through the brick, so each
-// force cell is fetched from L2 about once per brick rather than once per z
-// line.  The next iteration's dx and p are fetched (streamed, evict-first)
-// while the current one gathers.  Arithmetic and outputs are those of
-// body_readout<true, true>.  The force mesh is read through the read-only
-// path: it must not be written earlier in the same launch.
-constexpr int KB_THREADS = 256;
-
-template <int Z_, int IPX_, int X_>
-struct BrickShape {
-  static constexpr int Z = Z_;                          // z extent: Z / 32 warps per row
-  static constexpr int IPX = IPX_;                      // iterations per x plane
-  static constexpr int X = X_;                          // x planes per brick
-  static constexpr int RPI = (KB_THREADS / 32) / (Z / 32);   // y rows per iteration
-  static constexpr int Y = RPI * IPX;
-  static constexpr int ITERS = X * IPX;
-  static_assert(Z % 32 == 0 && (KB_THREADS / 32) % (Z / 32) == 0, "brick z extent");
-  static __host__ __device__ bool fits(int np) { return np % Z == 0 && np % Y == 0 && np % X == 0; }
-  static __host__ __device__ int blocks(int np) { return (np / X) * (np / Y) * (np / Z); }
-};
-
-template <class BS>
-__device__ __forceinline__ uint32_t brick_particle(int it, int bx, int by, int bz, int np) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int z = bz * BS::Z + (w % (BS::Z / 32)) * 32 + lane;
-  const int y = by * BS::Y + (it % BS::IPX) * BS::RPI + w / (BS::Z / 32);
-  const int x = bx * BS::X + it / BS::IPX;
-  return ((uint32_t)x * np + y) * np + z;
-}
-
-template <class BS, int TE = 16>
-__device__ __forceinline__ void body_kdk_brick(float* __restrict__ dx, float* __restrict__ p,
-                                               const float4* __restrict__ F, const Geom& g, size_t N,
-                                               const double* __restrict__ fac, int ik1, int ik2, int idr,
-                                               uint32_t* __restrict__ keys, uint32_t* __restrict__ tile_count,
-                                               int* __restrict__ err, int blk) {
-  const int np = g.np, nc = g.nc;
-  const int nbz = np / BS::Z, nby = np / BS::Y;
-  const int bz = blk % nbz, by = (blk / nbz) % nby, bx = blk / (nbz * nby);
-  const float K = (float)((ik1 >= 0 ? fac[ik1] : 0.0) + (ik2 >= 0 ? fac[ik2] : 0.0));
-  const float D = idr >= 0 ? (float)fac[idr] : 0.f;
-  float dn[3], pn[3];
-  {
-    const uint32_t i = brick_particle<BS>(0, bx, by, bz, np);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dn[a] = __ldcs(dx + a * N + i);
-      pn[a] = __ldcs(p + a * N + i);
-    }
-  }
-#pragma unroll 1
-  for (int it = 0; it < BS::ITERS; ++it) {
-    const uint32_t i = brick_particle<BS>(it, bx, by, bz, np);
-    float d[3] = {dn[0], dn[1], dn[2]}, pp[3] = {pn[0], pn[1], pn[2]};
-    if (it + 1 < BS::ITERS) {
-      const uint32_t inext = brick_particle<BS>(it + 1, bx, by, bz, np);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dn[a] = __ldcs(dx + a * N + inext);
-        pn[a] = __ldcs(p + a * N + inext);
-      }
-    }
-    int q[3], c[3];
-    float t[3];
-    lattice_node(i, g, q);
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-    const int cx1 = (c[0] + 1 == nc) ? 0 : c[0] + 1;
-    const int cy1 = (c[1] + 1 == nc) ? 0 : c[1] + 1;
-    const int cz1 = (c[2] + 1 == nc) ? 0 : c[2] + 1;
-    const size_t rx[2] = {(size_t)c[0] * nc * nc, (size_t)cx1 * nc * nc};
-    const int ry[2] = {c[1] * nc, cy1 * nc};
-    const int rz[2] = {c[2], cz1};
-    const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
-    float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const float4 v = __ldg(F + rx[b >> 2] + ry[(b >> 1) & 1] + rz[b & 1]);
-      const float wt = wx[b >> 2] * wy[(b >> 1) & 1] * wz[b & 1];
-      f[0] = fmaf(wt, v.x, f[0]);
-      f[1] = fmaf(wt, v.y, f[1]);
-      f[2] = fmaf(wt, v.z, f[2]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float pa = fmaf(K, f[a], pp[a]);
-      __stcs(p + a * N + i, pa);
-      d[a] = fmaf(D, pa, d[a]);
-      __stcs(dx + a * N + i, d[a]);
-    }
-    int tile = 0;
-    if (keys) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) ok &= cic_cell(d[a], q[a], nc, &c[a], &t[a]);
-      const uint32_t key = tile_key<TE>(c, g.nc / TE);
-      keys[i] = key;
-      tile = key >> (3 * TileC<TE>::LG);
-    }
-    if (!ok) atomicOr(err, ERR_NAN);
-    if (keys) warp_count(tile_count, tile, true);
-  }
-}
 
 }  // namespace fpm
