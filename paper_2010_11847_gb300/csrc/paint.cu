@@ -515,27 +515,7 @@ __device__ __forceinline__ float from_fix_signed(long long v, float inv_scale) {
 // (signed fixed point, unit 1/inv); nb: 8 words of shared memory.
 __device__ __forceinline__ void body_halo_vec(const unsigned long long* __restrict__ halo, const Geom& g, float inv,
                                               float* __restrict__ out, uint32_t* nb, int bx) {
-  const int nt = g.nt, nc = g.nc;
-  const int tc[3] = {bx / (nt * nt), (bx / nt) % nt, bx % nt};
-  if (threadIdx.x < 8) {
-    const int b = threadIdx.x;
-    const int x = tc[0] - (b >> 2), y = tc[1] - ((b >> 1) & 1), z = tc[2] - (b & 1);
-    nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < NFACE; k += blockDim.x) {
-    int l[3];
-    face_cell(k, l);
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int ox = b >> 2, oy = (b >> 1) & 1, oz = b & 1;
-      if ((ox && l[0]) || (oy && l[1]) || (oz && l[2])) continue;
-      sum += __ldcg(halo + (size_t)nb[b] * SHELL + shell_index(l[0] + TILE * ox, l[1] + TILE * oy, l[2] + TILE * oz));
-    }
-    out[((size_t)(tc[0] * TILE + l[0]) * nc + tc[1] * TILE + l[1]) * nc + tc[2] * TILE + l[2]] =
-        from_fix_signed((long long)sum, inv);
-  }
+  tile_face_sums(halo, g, out, nb, bx, [inv](unsigned long long v) { return from_fix_signed((long long)v, inv); });
 }
 
 // Readout transpose for one channel: out_c = sum_i W(x_i - c) v_i (no
@@ -584,17 +564,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
                      __float2int_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * vs));
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < (TILE - 1) * (TILE - 1) * (TILE - 1); k += blockDim.x) {
-    const int lx = 1 + k / ((TILE - 1) * (TILE - 1)), ly = 1 + (k / (TILE - 1)) % (TILE - 1), lz = 1 + k % (TILE - 1);
-    out[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
-        from_fix_signed((long long)acc_get(lo, hi, (lx * TILE1 + ly) * TILE1 + lz), inv);
-  }
-  unsigned long long* hb = halo + (size_t)tile * SHELL;
-  for (int s = threadIdx.x; s < SHELL; s += blockDim.x) {
-    int l[3];
-    shell_decode(s, l);
-    hb[s] = acc_get(lo, hi, (l[0] * TILE1 + l[1]) * TILE1 + l[2]);
-  }
+  paint_writeout_conv(Acc32{lo, hi}, o, tile, g, out, halo,
+                      [inv](unsigned long long v) { return from_fix_signed((long long)v, inv); });
   if (done) faces_last(done, halo, g, tile, sm, [&](int u) { body_halo_vec(halo, g, inv, out, sm, u); });
 }
 

@@ -352,24 +352,53 @@ __device__ __forceinline__ bool particle_local(const float* __restrict__ dx, siz
 }
 
 // Write the tile's interior cells (final) and its (TE+1)^3 shell (partials).
+// The tile's own TE^3 cells go one z row per TE lanes (blockDim.x a multiple
+// of TE): interior cells to rho, lower-face cells to the shell; then the
+// cells of the block with a coordinate equal to TE (the upper halo).
+template <class A, int TE = 16, class Conv>
+__device__ __forceinline__ void paint_writeout_conv(const A& acc, const int* o, int tile, const Geom& g,
+                                                    float* __restrict__ rho, unsigned long long* __restrict__ halo,
+                                                    Conv conv) {
+  constexpr int E = TE, E1 = TE + 1, LG = TileC<TE>::LG;
+  const int nc = g.nc;
+  unsigned long long* hb = halo + (size_t)tile * TileC<TE>::SHELL;
+  const int lz = threadIdx.x & (E - 1);
+  float* rb = rho + ((size_t)o[0] * nc + o[1]) * nc + o[2] + lz;
+  for (int r = threadIdx.x >> LG; r < E * E; r += blockDim.x >> LG) {
+    const int lx = r >> LG, ly = r & (E - 1);
+    const unsigned long long v = acc.get((lx * E1 + ly) * E1 + lz);
+    if (lx && ly && lz)
+      rb[(lx * nc + ly) * nc] = conv(v);
+    else
+      hb[shell_index<TE>(lx, ly, lz)] = v;
+  }
+  constexpr int UP = E1 * E1 + E * E1 + E * E;     // cells with a coordinate equal to E
+  for (int k = threadIdx.x; k < UP; k += blockDim.x) {
+    int l[3];
+    if (k < E1 * E1) {
+      l[0] = E;
+      l[1] = k / E1;
+      l[2] = k - l[1] * E1;
+    } else if (k < E1 * E1 + E * E1) {
+      const int r = k - E1 * E1;
+      l[0] = r / E1;
+      l[1] = E;
+      l[2] = r - l[0] * E1;
+    } else {
+      const int r = k - E1 * E1 - E * E1;
+      l[0] = r >> LG;
+      l[1] = r & (E - 1);
+      l[2] = E;
+    }
+    hb[shell_index<TE>(l[0], l[1], l[2])] = acc.get((l[0] * E1 + l[1]) * E1 + l[2]);
+  }
+}
+
 template <class A, int TE = 16>
 __device__ __forceinline__ void paint_writeout(const A& acc, const int* o, int tile, const Geom& g,
                                                float* __restrict__ rho, unsigned long long* __restrict__ halo) {
-  constexpr int E = TE, E1 = TE + 1;
-  const int nc = g.nc;
-  for (int k = threadIdx.x; k < (E - 1) * (E - 1) * (E - 1); k += blockDim.x) {
-    const int lx = 1 + k / ((E - 1) * (E - 1));
-    const int ly = 1 + (k / (E - 1)) % (E - 1);
-    const int lz = 1 + k % (E - 1);
-    rho[((size_t)(o[0] + lx) * nc + (o[1] + ly)) * nc + o[2] + lz] =
-        from_fix(acc.get((lx * E1 + ly) * E1 + lz), g.mass);
-  }
-  unsigned long long* hb = halo + (size_t)tile * TileC<TE>::SHELL;
-  for (int s = threadIdx.x; s < TileC<TE>::SHELL; s += blockDim.x) {
-    int l[3];
-    shell_decode<TE>(s, l);
-    hb[s] = acc.get((l[0] * E1 + l[1]) * E1 + l[2]);
-  }
+  const float mass = g.mass;
+  paint_writeout_conv<A, TE>(acc, o, tile, g, rho, halo, [mass](unsigned long long v) { return from_fix(v, mass); });
 }
 
 __device__ __forceinline__ void paint_writeout(const uint32_t* lo, const uint32_t* hi, const int* o, int tile,
@@ -458,11 +487,14 @@ __device__ __forceinline__ void face_cell(int k, int* l) {
   }
 }
 
-template <int TE = 16>
-__device__ __forceinline__ void body_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
-                                                float* __restrict__ rho, uint32_t* nb, int bx) {
+template <int TE = 16, class Conv>
+__device__ __forceinline__ void tile_face_sums(const unsigned long long* __restrict__ halo, const Geom& g,
+                                               float* __restrict__ rho, uint32_t* nb, int bx, Conv conv) {
   using C = TileC<TE>;
-  constexpr int E = TE;
+  constexpr int E = TE, E1 = TE + 1, LG = C::LG;
+  // shell offsets: x faces (lx = 0, E), y faces (lx in [1, E)), z faces (lx, ly in [1, E))
+  constexpr int SX = E1 * E1, SY = 2 * E1 * E1, SYE = SY + (E - 1) * E1, SZ = SY + 2 * (E - 1) * E1,
+                SZE = SZ + (E - 1) * (E - 1);
   const int nc = g.nc, nt = nc / TE;
   const int tile = bx;
   const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
@@ -472,18 +504,43 @@ __device__ __forceinline__ void body_paint_halo(const unsigned long long* __rest
     nb[b] = ((x < 0 ? x + nt : x) * nt + (y < 0 ? y + nt : y)) * nt + (z < 0 ? z + nt : z);
   }
   __syncthreads();
+  // partial of cell s of the shell of lower neighbour b (bit 2: -x, bit 1: -y, bit 0: -z)
+  auto H = [&](int b, int s) { return __ldcg(halo + (size_t)nb[b] * C::SHELL + s); };
+  float* rt = rho + ((size_t)tc[0] * E * nc + tc[1] * E) * nc + tc[2] * E;
   for (int k = threadIdx.x; k < C::NFACE; k += blockDim.x) {
-    int l[3];
-    face_cell<TE>(k, l);
-    unsigned long long sum = 0;
-  #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int bx = b >> 2, by = (b >> 1) & 1, bz = b & 1;
-      if ((bx && l[0]) || (by && l[1]) || (bz && l[2])) continue;
-      sum += __ldcg(halo + (size_t)nb[b] * C::SHELL + shell_index<TE>(l[0] + E * bx, l[1] + E * by, l[2] + E * bz));
+    unsigned long long sum;
+    int l0, l1, l2;
+    if (k < E * E) {                       // x = 0 face
+      l0 = 0;
+      l1 = k >> LG;
+      l2 = k & (E - 1);
+      sum = H(0, l1 * E1 + l2) + H(4, SX + l1 * E1 + l2);
+      if (l1 == 0) sum += H(2, E * E1 + l2) + H(6, SX + E * E1 + l2);
+      if (l2 == 0) sum += H(1, l1 * E1 + E) + H(5, SX + l1 * E1 + E);
+      if (l1 == 0 && l2 == 0) sum += H(3, E * E1 + E) + H(7, SX + E * E1 + E);
+    } else if (k < E * E + (E - 1) * E) {  // y = 0 face, lx >= 1
+      const int r = k - E * E;
+      l0 = 1 + (r >> LG);
+      l1 = 0;
+      l2 = r & (E - 1);
+      sum = H(0, SY + (l0 - 1) * E1 + l2) + H(2, SYE + (l0 - 1) * E1 + l2);
+      if (l2 == 0) sum += H(1, SY + (l0 - 1) * E1 + E) + H(3, SYE + (l0 - 1) * E1 + E);
+    } else {                               // z = 0 face, lx, ly >= 1
+      const int r = k - E * E - (E - 1) * E;
+      l0 = 1 + r / (E - 1);
+      l1 = 1 + r % (E - 1);
+      l2 = 0;
+      sum = H(0, SZ + (l0 - 1) * (E - 1) + (l1 - 1)) + H(1, SZE + (l0 - 1) * (E - 1) + (l1 - 1));
     }
-    rho[((size_t)(tc[0] * E + l[0]) * nc + tc[1] * E + l[1]) * nc + tc[2] * E + l[2]] = from_fix(sum, g.mass);
+    rt[(l0 * nc + l1) * nc + l2] = conv(sum);
   }
+}
+
+template <int TE = 16>
+__device__ __forceinline__ void body_paint_halo(const unsigned long long* __restrict__ halo, Geom g,
+                                                float* __restrict__ rho, uint32_t* nb, int bx) {
+  const float mass = g.mass;
+  tile_face_sums<TE>(halo, g, rho, nb, bx, [mass](unsigned long long v) { return from_fix(v, mass); });
 }
 
 // Faces summed by the last contributor.  A tile's lower-face cells receive
@@ -501,17 +558,22 @@ __device__ __forceinline__ void faces_last(uint32_t* __restrict__ done, const un
   const int nt = g.nt;
   uint32_t* list = sm + 8;           // up to 8 completed tiles (sm[0..7]: the face sum's neighbours)
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
-    uint32_t nl = 0;
-    __threadfence();
-    for (int b = 0; b < 8; ++b) {
+  if (threadIdx.x < 32) {
+    // lanes 0..7 count the block toward the 8 tiles T + {0,1}^3 at once
+    const int b = threadIdx.x;
+    bool last = false;
+    uint32_t u = 0;
+    if (b < 8) {
+      const int tc[3] = {tile / (nt * nt), (tile / nt) % nt, tile % nt};
       const int x = tc[0] + (b >> 2), y = tc[1] + ((b >> 1) & 1), z = tc[2] + (b & 1);
-      const int u = ((x == nt ? 0 : x) * nt + (y == nt ? 0 : y)) * nt + (z == nt ? 0 : z);
-      if (atomicAdd(done + u, 1u) == 7u) list[nl++] = (uint32_t)u;
+      u = (uint32_t)(((x == nt ? 0 : x) * nt + (y == nt ? 0 : y)) * nt + (z == nt ? 0 : z));
+      __threadfence();
+      last = atomicAdd(done + u, 1u) == 7u;
+      __threadfence();
     }
-    __threadfence();
-    sm[16] = nl;
+    const unsigned m = __ballot_sync(0xffffffffu, last);
+    if (last) list[__popc(m & ((1u << b) - 1u))] = u;
+    if (b == 0) sm[16] = __popc(m);
   }
   __syncthreads();
   const uint32_t nl = sm[16];
