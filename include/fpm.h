@@ -180,13 +180,21 @@ int fpm_readout(fpm_plan* plan, const float* F, const float* dx, float* f_out,
  * one.  The coefficients are computed on the GPU in FP64.  ckpt (NULL to
  * skip): float[nsteps+1][3][np^3], receives dx at every a_k (the momenta
  * are not needed to reverse the steps: the force depends on dx only).
- * fckpt (NULL to skip): float[nsteps+1][4 nc^3], receives the force mesh of
- * every a_k in the plan's internal layout (float4 per cell on power-of-two
- * meshes, else [3][nc^3]); fpm_kdk_adj then reuses it instead of
- * recomputing the forces (the forces are computed straight into it: no
- * extra traffic, 4 nc^3 floats of memory per stage). */
+ * fckpt (NULL to skip): float[nsteps+1][fpm_force_ckpt_floats(plan)],
+ * receives for every a_k the force mesh in the plan's internal layout
+ * (float4 per cell on power-of-two meshes, else [3][nc^3]) and the tile
+ * buckets of that stage's particles; fpm_kdk_adj then reuses both instead
+ * of recomputing the forces and re-sorting the particles (both are written
+ * straight into the checkpoint by the kernels that make them: no extra
+ * traffic).  Its contents are internal: only fpm_kdk_adj reads them. */
 int fpm_kdk(fpm_plan* plan, float* dx, float* p, const double* a, int nsteps,
             float* ckpt, float* fckpt, void* stream);
+
+/* Floats per stage of fpm_kdk's force checkpoint fckpt: 4 nc^3 for the
+ * force mesh plus np^3 + np^3/2 + (nc/16)^3 + 1 for the tile buckets,
+ * rounded up to a multiple of 64 (0 for a NULL plan).  Not in the paper: a
+ * memory-for-time choice of the reverse pass (Sec. 5 stores the states). */
+int64_t fpm_force_ckpt_floats(const fpm_plan* plan);
 
 /* Binned power spectrum (Eq. 10's ingredient) of mesh field `a`, or the
  * cross spectrum of `a` and `b` (b may be NULL):
@@ -252,10 +260,11 @@ int fpm_force_adj(fpm_plan* plan, const float* g_F, float* g_rho, void* stream);
  * holds the cotangent of the final dx and g_p_in (nullable: zero, e.g. a
  * loss on the density alone) that of the final p; on return g_dx and g_p
  * (required, may equal g_p_in) hold the cotangents of the initial dx and p.
- * Each reverse step buckets the checkpoint's particles by tile and takes its
- * force from fckpt (or recomputes paint and force), then applies the drift
- * transpose and the transposed force Jacobian (readout, force and paint
- * transposes).  The result is bitwise the same either way. */
+ * Each reverse step takes the stage's force and tile buckets from fckpt (as
+ * written by the fpm_kdk call over the same a; NULL: recomputes paint and
+ * force), then applies the drift transpose and the transposed force
+ * Jacobian (readout, force and paint transposes).  The result is bitwise
+ * the same either way. */
 int fpm_kdk_adj(fpm_plan* plan, const float* ckpt, const float* fckpt, const double* a, int nsteps,
                 float* g_dx, const float* g_p_in, float* g_p, void* stream);
 

@@ -17,16 +17,18 @@ import torch
 from .binding import Plan
 
 
-# Force checkpoints (the forward's force mesh at every stage) spare the
-# reverse pass a paint and a force per step; they are kept when they fit in
-# the free device memory with this margin to spare.
+# Force checkpoints (the forward's force mesh and tile buckets at every
+# stage) spare the reverse pass a paint, a force and a sort per step; they
+# are kept when they fit in the device memory that is free or held unused by
+# torch's caching allocator, with this margin to spare.
 FORCE_CKPT_MARGIN_BYTES = 8 << 30
 
 
 def _force_checkpoints(plan: Plan, nstages: int, device):
     need = nstages * plan.force_ckpt_floats * 4
     free, _ = torch.cuda.mem_get_info(device)
-    if need + FORCE_CKPT_MARGIN_BYTES > free:
+    cached = torch.cuda.memory_reserved(device) - torch.cuda.memory_allocated(device)
+    if need + FORCE_CKPT_MARGIN_BYTES > free + cached:
         return None
     return torch.empty(nstages, plan.force_ckpt_floats, device=device)
 

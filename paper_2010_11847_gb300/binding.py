@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
     L.fpm_force.argtypes = [vp, vp, vp, vp]
     L.fpm_readout.argtypes = [vp, vp, vp, vp, vp]
     L.fpm_kdk.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
+    L.fpm_force_ckpt_floats.argtypes = [vp]
+    L.fpm_force_ckpt_floats.restype = i64
     L.fpm_power.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fpm_status.argtypes = [vp, vp]
     L.fpm_strerror.argtypes = [i]
@@ -235,7 +237,8 @@ class Plan:
 
     def kdk(self, dx, p, a, ckpt=None, fckpt=None, stream=None):
         """KDK steps over the scale factors a; ckpt [len(a), 3, N] receives dx
-        at every stage, fckpt [len(a), force_ckpt_floats] the force meshes."""
+        at every stage, fckpt [len(a), force_ckpt_floats] the force meshes and
+        tile buckets."""
         a = _host_f64(a).ravel()
         _check("fpm_kdk", lib().fpm_kdk(self._h, _ptr(dx), _ptr(p), a.ctypes.data, a.size - 1, _ptr(ckpt),
                                         _ptr(fckpt), _stream(stream)))
@@ -243,8 +246,9 @@ class Plan:
 
     @property
     def force_ckpt_floats(self) -> int:
-        """Floats per stage of a force checkpoint (4 nc^3)."""
-        return 4 * self.M
+        """Floats per stage of a force checkpoint (the force mesh, 4 nc^3, and
+        the stage's tile buckets)."""
+        return int(lib().fpm_force_ckpt_floats(self._h))
 
     def power(self, a, b=None, stream=None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
         nb = self.nc // 2

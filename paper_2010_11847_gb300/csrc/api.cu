@@ -244,6 +244,24 @@ int paint_impl(fpm_plan* p, const float* dx, float* rho, uint32_t* keys, uint32_
   return sort_paint_impl(p, c, dx, rho, perm, s);
 }
 
+// One stage of a force checkpoint: the force mesh (4 nc^3 floats), then the
+// tile buckets of the stage's positions -- items (np^3 u32), in-tile cells
+// (np^3 u16), tile starts (ntiles + 1 u32) -- padded to 64 floats.
+size_t ckpt_stage_floats(const fpm_plan* p) {
+  const size_t f = 4 * p->M + p->N + (p->N + 1) / 2 + (size_t)p->pc.ntiles + 1;
+  return (f + 63) & ~(size_t)63;
+}
+
+// The plan's paint context with its buckets in stage k of fckpt.
+PaintCtx stage_ctx(const fpm_plan* p, const float* fckpt, int k) {
+  PaintCtx c = p->pc;
+  float* b = const_cast<float*>(fckpt) + (size_t)k * ckpt_stage_floats(p) + 4 * p->M;
+  c.items = reinterpret_cast<uint32_t*>(b);
+  c.cells = reinterpret_cast<uint16_t*>(b + p->N);
+  c.tile_start = reinterpret_cast<uint32_t*>(b + p->N + (p->N + 1) / 2);
+  return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -460,26 +478,37 @@ int fpm_kdk(fpm_plan* p, float* dx, float* mom, const double* a, int nsteps, flo
   }));
   p->fac_pts = pts;
   const size_t N = p->N;
-  // the force of stage k is computed straight into its checkpoint slot when
-  // the caller keeps them (the reverse pass then reuses it)
-  auto Fk = [&](int k) { return fckpt ? fckpt + (size_t)k * 4 * p->M : p->F; };
+  // the force of stage k is computed straight into its checkpoint slot, and
+  // the stage's tile buckets are written there by its sort
+  auto Fk = [&](int k) { return fckpt ? fckpt + (size_t)k * ckpt_stage_floats(p) : p->F; };
+  auto Ck = [&](int k) { return fckpt ? stage_ctx(p, fckpt, k) : p->pc; };
+  // with checkpoints and the brick readout, the drift of step k writes
+  // straight into stage k+1 of ckpt and the steps run on the checkpoints
+  // (the closing kick writes dx): no copies
+  const bool in_ckpt = ckpt && kdk_brick_fits(p->pc, p->f4);
+  auto X = [&](int k) { return in_ckpt ? ckpt + (size_t)k * 3 * N : dx; };
   if (ckpt) FPM_CUDA_TRY(cudaMemcpyAsync(ckpt, dx, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  FPM_TRY(paint_impl(p, dx, p->rho, nullptr, nullptr, s));
+  {
+    const PaintCtx c0 = Ck(0);
+    FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c0, dx, s); }));
+    FPM_TRY(sort_paint_impl(p, c0, dx, p->rho, nullptr, s));
+  }
   FPM_TRY(force_impl(p, p->rho, Fk(0), s, p->f4));
   for (int k = 0; k < nsteps; ++k) {
     // closing kick of step k-1 and opening kick of step k share the force at a_k
     const int ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
     FPM_TRY(timed(p, FPM_K_KDK, 1, s, [&] {
-      return launch_kdk(p->pc, dx, mom, Fk(k), p->f4, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s);
+      return launch_kdk(p->pc, X(k), mom, Fk(k), p->f4, p->d_fac, 3 * k + 0, ik2, 3 * k + 1, true, s, X(k + 1));
     }));
-    if (ckpt)
+    if (ckpt && !in_ckpt)
       FPM_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(k + 1) * 3 * N, dx, 3 * N * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s));
-    FPM_TRY(sort_paint_impl(p, p->pc, dx, p->rho, nullptr, s));
+    FPM_TRY(sort_paint_impl(p, Ck(k + 1), X(k + 1), p->rho, nullptr, s));
     FPM_TRY(force_impl(p, p->rho, Fk(k + 1), s, p->f4));
   }
   return timed(p, FPM_K_KDK, 1, s, [&] {
-    return launch_kdk(p->pc, dx, mom, Fk(nsteps), p->f4, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s);
+    return launch_kdk(p->pc, X(nsteps), mom, Fk(nsteps), p->f4, p->d_fac, 3 * (nsteps - 1) + 2, -1, -1, false, s,
+                      dx);
   });
 }
 
@@ -631,6 +660,8 @@ const char* fpm_kernel_class_name(int cls) {
 
 int64_t fpm_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int64_t fpm_force_ckpt_floats(const fpm_plan* p) { return p ? (int64_t)ckpt_stage_floats(p) : 0; }
+
 // ---------------------------------------------------------------- adjoints
 static constexpr int CHI_PARTIALS = 1024;
 
@@ -677,20 +708,36 @@ static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream
 
 // gx += J_f(x)^T v at the positions x whose paint (buckets) and force
 // meshes (p->F, interleaved when p->f4) are current; uses p->rho as scratch.
-static int force_jt_impl(fpm_plan* p, const float* x, const float* v, float* gx, const float* F, cudaStream_t s) {
-  FPM_TRY(timed(p, FPM_K_PAINT, p->pc.tile_done ? 4 : 7, s,
-                [&] { return launch_paint_vec(p->pc, x, v, p->vmax, p->gF, s); }));
-  FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
-  return timed(p, FPM_K_READOUT, 1, s,
-               [&] { return launch_gather_adj(p->pc, x, p->rho, F, p->f4, v, gx, true, s); });
-}
+// The next reverse step's drift and kick transposes, when the transposed
+// gather can apply them on the fly (dk_idr >= 0).
+struct NextDriftKick {
+  int idr = -1, ik1 = -1, ik2 = -1;
+};
 
-// Tile buckets (and in-tile cells) of positions x, without the paint.
-static int sort_impl(fpm_plan* p, const float* x, cudaStream_t s) {
-  PaintCtx c = p->pc;
-  FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, x, s); }));
-  FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
-  return timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); });
+// gx += J^T v at positions x (paint, force and readout transposes).  With
+// vmax_ready the vector paint takes max |v| from p->vmax.  Returns (in
+// *fused) whether the gather also applied `next` to (gx, gp) and left v
+// and max |v| for the next step.
+static int force_jt_impl(fpm_plan* p, const PaintCtx& c, const float* x, float* v, float* gx, const float* F,
+                         cudaStream_t s, bool vmax_ready = false, NextDriftKick next = {}, float* gp = nullptr,
+                         bool* fused = nullptr) {
+  if (fused) *fused = false;
+  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s,
+                [&] { return launch_paint_vec(c, x, v, p->vmax, p->gF, s, vmax_ready); }));
+  FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
+  if (next.idr >= 0 && gp && fused) {
+    const int r = timed(p, FPM_K_READOUT, 1, s, [&] {
+      return launch_gather_adj_dk(c, x, p->rho, F, p->f4, v, gx, gp, p->d_fac, next.idr, next.ik1, next.ik2,
+                                  p->vmax, s);
+    });
+    if (r == FPM_OK) {
+      *fused = true;
+      return FPM_OK;
+    }
+    if (r != FPM_ENOTIMPL) return r;
+  }
+  return timed(p, FPM_K_READOUT, 1, s,
+               [&] { return launch_gather_adj(c, x, p->rho, F, p->f4, v, gx, true, s); });
 }
 
 extern "C" {
@@ -778,32 +825,47 @@ int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const float* fckpt, const double
   } else {     // the loss does not depend on the final momenta: start from zero
     FPM_CUDA_TRY(cudaMemsetAsync(gp, 0, N3 * sizeof(float), s));
   }
-  // the force at stage k and the tile buckets of x_k: from the forward's
-  // force checkpoint (buckets only), or recomputed (paint + force)
+  // the force at stage k and the tile buckets of x_k: both from the
+  // forward's force checkpoint, or recomputed (paint + force)
   const float* Fk = p->F;
+  PaintCtx Ck = p->pc;
   auto prepare = [&](int k, const float* x) -> int {
     if (fckpt) {
-      Fk = fckpt + (size_t)k * 4 * p->M;
-      return sort_impl(p, x, s);
+      Fk = fckpt + (size_t)k * ckpt_stage_floats(p);
+      Ck = stage_ctx(p, fckpt, k);
+      return FPM_OK;
     }
     Fk = p->F;
+    Ck = p->pc;
     FPM_TRY(paint_impl(p, x, p->rho, nullptr, nullptr, s));
     return force_impl(p, p->rho, p->F, s, p->f4);
   };
+  // drift transpose of step k, then the merged kick at x_k (opening kick of
+  // step k and closing kick of step k-1 share the force at a_k)
+  auto drift_kick = [](int k) {
+    NextDriftKick d;
+    d.idr = 3 * k + 1;
+    d.ik1 = 3 * k + 0;
+    d.ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
+    return d;
+  };
+  bool ready = false;   // v = vbuf and max |v| of the next step already applied by the last gather
   if (g_p_in) {   // closing half kick at a_n: gx += J^T(x_n) (K gp)
     const float* xn = ckpt + (size_t)nsteps * N3;
     FPM_TRY(prepare(nsteps, xn));
     FPM_TRY(launch_scale_copy(gp, p->vbuf, N3, p->d_fac, 3 * (nsteps - 1) + 2, s));
-    FPM_TRY(force_jt_impl(p, xn, p->vbuf, g_dx, Fk, s));
+    FPM_TRY(force_jt_impl(p, Ck, xn, p->vbuf, g_dx, Fk, s, false, drift_kick(nsteps - 1), gp, &ready));
   }
   for (int k = nsteps - 1; k >= 0; --k) {
     const float* xk = ckpt + (size_t)k * N3;
-    // drift transpose, then the merged kick at x_k (opening kick of step k
-    // and closing kick of step k-1 share the force at a_k)
-    FPM_TRY(launch_adj_drift_kick(g_dx, gp, p->vbuf, N3, p->d_fac, 3 * k + 1, 3 * k + 0,
-                                  k > 0 ? 3 * (k - 1) + 2 : -1, s));
+    if (!ready) {
+      const NextDriftKick d = drift_kick(k);
+      FPM_TRY(launch_adj_drift_kick(g_dx, gp, p->vbuf, N3, p->d_fac, d.idr, d.ik1, d.ik2, s));
+    }
     FPM_TRY(prepare(k, xk));
-    FPM_TRY(force_jt_impl(p, xk, p->vbuf, g_dx, Fk, s));
+    const bool vmax_ready = ready;
+    FPM_TRY(force_jt_impl(p, Ck, xk, p->vbuf, g_dx, Fk, s, vmax_ready, k > 0 ? drift_kick(k - 1) : NextDriftKick{},
+                          gp, &ready));
   }
   g_launches += 1 + 2 * nsteps;
   return FPM_OK;

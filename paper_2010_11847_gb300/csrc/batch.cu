@@ -199,9 +199,9 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
           const float4* F4p = reinterpret_cast<const float4*>(d.F);
           if (d.te == 8) {
             if (d.f4 && d.rshape == 1)
-              body_kdk_brick<Brick32, 8>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+              body_kdk_brick<Brick32, 8>(d.dx, d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
             else if (d.f4 && d.rshape == 2)
-              body_kdk_brick<Brick64, 8>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+              body_kdk_brick<Brick64, 8>(d.dx, d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
             else if (d.f4)
               body_readout<true, true, true, 8>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
                                                 d.tile_count, d.err, a.ro_iters, local);
@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
                                                  d.tile_count, d.err, a.ro_iters, local);
           } else {
             if (d.f4 && d.rshape == 1)
-              body_kdk_brick<Brick32>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+              body_kdk_brick<Brick32>(d.dx, d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
             else if (d.f4 && d.rshape == 2)
-              body_kdk_brick<Brick64>(d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
+              body_kdk_brick<Brick64>(d.dx, d.dx, d.p, F4p, d.g, d.N, d.fac, ik1, ik2, idr, keys, d.tile_count, d.err, local);
             else if (d.f4)
               body_readout<true, true, true>(d.dx, d.p, d.F, d.g, d.N, d.M, d.fac, ik1, ik2, idr, nullptr, keys,
                                              d.tile_count, d.err, a.ro_iters, local);

@@ -106,18 +106,31 @@ int launch_paint_tiles(const PaintCtx& c, const float* dx, float* rho, uint32_t*
 int launch_perm_big(const PaintCtx& c, uint32_t* perm, cudaStream_t s);
 int launch_halo(const PaintCtx& c, float* rho, cudaStream_t s);
 int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_out, cudaStream_t s);
+// dx_out: where the drifted displacements go (null: dx itself; a separate
+// buffer needs the brick traversal)
 int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
-               int ik2, int idr, bool emit_keys, cudaStream_t s);
+               int ik2, int idr, bool emit_keys, cudaStream_t s, float* dx_out = nullptr);
+// readout.cu: whether launch_kdk takes the brick traversal (and so accepts a
+// separate dx_out)
+bool kdk_brick_fits(const PaintCtx& c, bool f4);
 // readout.cu: the brick traversal of the fused readout (interleaved float4
 // force, lattice divisible by the brick); keys == nullptr emits no keys.
-int launch_kdk_brick(const PaintCtx& c, float* dx, float* p, const float4* F, const double* fac, int ik1,
-                     int ik2, int idr, uint32_t* keys, cudaStream_t s);
+int launch_kdk_brick(const PaintCtx& c, const float* dx, float* dx_out, float* p, const float4* F, const double* fac,
+                     int ik1, int ik2, int idr, uint32_t* keys, cudaStream_t s);
 
 // paint.cu: adjoints at fixed positions
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
                       const float* v, float* g_dx, bool accumulate, cudaStream_t s);
+// vmax_ready: *vmax already holds max |v| (bit pattern), e.g. from launch_gather_adj_dk
 int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
-                     cudaStream_t s);
+                     cudaStream_t s, bool vmax_ready = false);
+// launch_gather_adj (accumulating, float4 force, brick lattices) followed per
+// particle by the next reverse step's drift and kick transposes (gp += D
+// g_dx, v = K gp in place) and max |v| into *vmax; FPM_ENOTIMPL where the
+// lattice or layout has no brick gather (the caller then runs them apart).
+int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* v,
+                         float* g_dx, float* gp, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
+                         cudaStream_t s);
 
 // adjoint.cu: spectral adjoints (power-of-two sizes) and elementwise steps
 enum SrcKernel : int {

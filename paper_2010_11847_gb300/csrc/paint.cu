@@ -326,12 +326,14 @@ int launch_readout(const PaintCtx& c, const float* F, const float* dx, float* f_
 
 // F is [3][M] (f4 = false) or interleaved float4 [M] (f4 = true).
 int launch_kdk(const PaintCtx& c, float* dx, float* p, const float* F, bool f4, const double* fac, int ik1,
-               int ik2, int idr, bool emit_keys, cudaStream_t s) {
+               int ik2, int idr, bool emit_keys, cudaStream_t s, float* dx_out) {
   if (emit_keys) FPM_CUDA_TRY(cudaMemsetAsync(c.tile_count, 0, sizeof(uint32_t) * c.ntiles, s));
   const int it = readout_iters(c.N);
   uint32_t* keys = emit_keys ? c.keys : nullptr;
   if (f4 && KDK_BRICK && KdkBrick::fits(c.g.np))
-    return launch_kdk_brick(c, dx, p, reinterpret_cast<const float4*>(F), fac, ik1, ik2, idr, keys, s);
+    return launch_kdk_brick(c, dx, dx_out ? dx_out : dx, p, reinterpret_cast<const float4*>(F), fac, ik1, ik2, idr,
+                            keys, s);
+  if (dx_out && dx_out != dx) return FPM_EINVAL;
   if (f4)
     k_readout<true, true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, p, F, c.g, c.N, c.M, fac, ik1, ik2, idr,
                                                                  nullptr, keys, c.tile_count, c.err, it);
@@ -416,13 +418,33 @@ __global__ void __launch_bounds__(256) k_gather_adj(const float* __restrict__ dx
 // The same transposed gather over the Lagrangian bricks of the fused
 // readout (KdkBrick): the mesh corners a CTA's particles touch stay in L1
 // while it marches through its brick.  Identical arithmetic per particle.
+//
+// With a drift-kick tail (dk.gp non-null) each particle then applies the
+// next reverse step's drift and kick transposes to its new cotangent, as
+// k_adj_drift_kick does (gp += D g_dx; v = K gp, v overwritten in place),
+// and the block records max |v| for the next vector paint.
+struct DriftKickTail {
+  float* gp = nullptr;
+  const double* fac = nullptr;
+  int idr = -1, ik1 = -1, ik2 = -1;
+  unsigned* vmax = nullptr;        // zeroed by the launcher
+};
+
 template <bool F4>
 __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __restrict__ dx, Geom g, size_t N,
                                                                  size_t M, const float* __restrict__ g_rho,
                                                                  const float* __restrict__ F,
-                                                                 const float* __restrict__ v,
-                                                                 float* __restrict__ g_dx, int accumulate) {
+                                                                 float* __restrict__ v,
+                                                                 float* __restrict__ g_dx, int accumulate,
+                                                                 DriftKickTail dk) {
   using BS = KdkBrick;
+  __shared__ unsigned s_max[KB_THREADS / 32];
+  float Dn = 0.f, Kn = 0.f;
+  if (dk.gp) {
+    Dn = (float)dk.fac[dk.idr];
+    Kn = (float)(dk.fac[dk.ik1] + (dk.ik2 >= 0 ? dk.fac[dk.ik2] : 0.0));
+  }
+  unsigned vm = 0;
   const int np = g.np, nc = g.nc;
   const int nbz = np / BS::Z, nby = np / BS::Y;
   const int blk = blockIdx.x;
@@ -475,7 +497,27 @@ __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __
       gsum[2] = fmaf((bz_ ? 1.f : -1.f) * wx * wy, s, gsum[2]);
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) __stcs(g_dx + a * N + i, accumulate ? __ldcs(g_dx + a * N + i) + gsum[a] : gsum[a]);
+    for (int a = 0; a < 3; ++a) {
+      const float gx = accumulate ? __ldcs(g_dx + a * N + i) + gsum[a] : gsum[a];
+      __stcs(g_dx + a * N + i, gx);
+      if (dk.gp) {
+        const float gq = fmaf(Dn, gx, __ldcs(dk.gp + a * N + i));
+        __stcs(dk.gp + a * N + i, gq);
+        const float vq = Kn * gq;
+        __stcs(v + a * N + i, vq);
+        vm = max(vm, __float_as_uint(fabsf(vq)));
+      }
+    }
+  }
+  if (dk.gp) {
+    for (int off = 16; off; off >>= 1) vm = max(vm, __shfl_xor_sync(0xffffffffu, vm, off));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = vm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned m = 0;
+      for (int w = 0; w < KB_THREADS / 32; ++w) m = max(m, s_max[w]);
+      atomicMax(dk.vmax, m);
+    }
   }
 }
 
@@ -608,12 +650,13 @@ int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, co
                       const float* v, float* g_dx, bool accumulate, cudaStream_t s) {
   const int it = readout_iters(c.N);
   if (KDK_BRICK && KdkBrick::fits(c.g.np)) {
+    float* vv = const_cast<float*>(v);     // read only without a drift-kick tail
     if (f4)
-      k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx,
-                                                                              accumulate);
+      k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, vv, g_dx,
+                                                                              accumulate, DriftKickTail{});
     else
-      k_gather_adj_brick<false><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v,
-                                                                               g_dx, accumulate);
+      k_gather_adj_brick<false><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, vv,
+                                                                               g_dx, accumulate, DriftKickTail{});
   } else if (f4)
     k_gather_adj<true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate, it);
   else
@@ -625,11 +668,31 @@ int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, co
 
 // Readout transpose of the 3 channels of v into meshes out[3][M]; the tile
 // buckets must hold the positions dx (a paint of dx ran last on this ctx).
-int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
-                     cudaStream_t s) {
+int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* v,
+                         float* g_dx, float* gp, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
+                         cudaStream_t s) {
+  if (!(KDK_BRICK && KdkBrick::fits(c.g.np) && f4)) return FPM_ENOTIMPL;
   FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
-  k_maxabs<<<1024, 256, 0, s>>>(v, 3 * c.N, vmax);
+  DriftKickTail dk;
+  dk.gp = gp;
+  dk.fac = fac;
+  dk.idr = idr;
+  dk.ik1 = ik1;
+  dk.ik2 = ik2;
+  dk.vmax = vmax;
+  k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, 1,
+                                                                          dk);
   FPM_CUDA_TRY(cudaGetLastError());
+  return FPM_OK;
+}
+
+int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
+                     cudaStream_t s, bool vmax_ready) {
+  if (!vmax_ready) {
+    FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
+    k_maxabs<<<1024, 256, 0, s>>>(v, 3 * c.N, vmax);
+    FPM_CUDA_TRY(cudaGetLastError());
+  }
   for (int ch = 0; ch < 3; ++ch) {
     k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vmax,
                                                 out + ch * c.M, c.halo, cells_of(c), c.tile_done);

@@ -17,7 +17,9 @@ namespace fpm {
 // line.  The next iteration's dx and p are fetched (streamed, evict-first)
 // while the current one gathers.  Arithmetic and outputs are those of
 // body_readout<true, true>.  The force mesh is read through the read-only
-// path: it must not be written earlier in the same launch.
+// path: it must not be written earlier in the same launch.  The drifted
+// displacements go to dx_out, which may be dx itself (each particle is read
+// before it is written, by the same thread).
 constexpr int KB_THREADS = 256;
 
 template <int Z_, int IPX_, int X_>
@@ -43,7 +45,7 @@ __device__ __forceinline__ uint32_t brick_particle(int it, int bx, int by, int b
 }
 
 template <class BS, int TE = 16>
-__device__ __forceinline__ void body_kdk_brick(float* __restrict__ dx, float* __restrict__ p,
+__device__ __forceinline__ void body_kdk_brick(const float* dx, float* dx_out, float* __restrict__ p,
                                                const float4* __restrict__ F, const Geom& g, size_t N,
                                                const double* __restrict__ fac, int ik1, int ik2, int idr,
                                                uint32_t* __restrict__ keys, uint32_t* __restrict__ tile_count,
@@ -101,7 +103,7 @@ __device__ __forceinline__ void body_kdk_brick(float* __restrict__ dx, float* __
       const float pa = fmaf(K, f[a], pp[a]);
       __stcs(p + a * N + i, pa);
       d[a] = fmaf(D, pa, d[a]);
-      __stcs(dx + a * N + i, d[a]);
+      __stcs(dx_out + a * N + i, d[a]);
     }
     int tile = 0;
     if (keys) {

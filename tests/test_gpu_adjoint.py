@@ -213,22 +213,27 @@ def test_differentiable_config_gradient(torch_mod):
 
 @pytest.mark.parametrize("np_,nc,reverse", [(32, 64, True), (32, 32, True), (48, 96, False)])
 def test_force_checkpoints_give_the_same_bits(torch_mod, np_, nc, reverse):
-    """Keeping the forward's force meshes (fckpt) changes nothing but the
-    work: the same forward state and checkpoints (float4 and planar force
-    meshes), and the same cotangents as the reverse pass that recomputes the
-    forces (the reverse pass runs on power-of-two meshes)."""
+    """Keeping the forward's force meshes and tile buckets (fckpt) changes
+    nothing but the work: the same forward state and checkpoints (float4 and
+    planar force meshes) as without them and as without any checkpoint, and
+    the same cotangents as the reverse pass that recomputes the forces and
+    buckets (the reverse pass runs on power-of-two meshes)."""
     torch = torch_mod
     stages = np.linspace(0.1, 0.7, 4)
     pl = plan(np_, nc)
     lk = pl.linear_field(dev(inputs.white_noise(np_, 9), torch))
     dx, p = pl.lpt(lk, float(stages[0]), 2)
     dx2, p2 = dx.clone(), p.clone()
+    dx3, p3 = dx.clone(), p.clone()
     ck = torch.empty(len(stages), 3, pl.N, device="cuda")
     ck2 = torch.empty_like(ck)
     fck = torch.empty(len(stages), pl.force_ckpt_floats, device="cuda")
     pl.kdk(dx, p, stages, ckpt=ck)
     pl.kdk(dx2, p2, stages, ckpt=ck2, fckpt=fck)
+    pl.kdk(dx3, p3, stages)                     # no checkpoints: the steps run on dx itself
     assert torch.equal(dx, dx2) and torch.equal(p, p2) and torch.equal(ck, ck2)
+    assert torch.equal(dx, dx3) and torch.equal(p, p3)
+    assert torch.equal(ck[-1], dx3)              # the closing kick does not move the particles
     if not reverse:
         return
     gdx = dev(inputs.random_displacements(np_, 1.0, 6), torch)
