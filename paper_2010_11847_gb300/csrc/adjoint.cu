@@ -212,7 +212,8 @@ int launch_adam(float* x, const float* g, float* m, float* v, size_t n, float gs
 }
 
 // ------------------------------------------------------------ reverse kick / drift
-// gp += D gx (drift transpose), then v = K gp with K = fac[ik1] (+ fac[ik2]).
+// gp += D gx (drift transpose), then v = K gp with K = fac[ik1] (+ fac[ik2])
+// (v null: gp only).
 __global__ void k_adj_drift_kick(float* __restrict__ gx, float* __restrict__ gp, float* __restrict__ v, size_t n,
                                  const double* __restrict__ fac, int idr, int ik1, int ik2) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -221,7 +222,7 @@ __global__ void k_adj_drift_kick(float* __restrict__ gx, float* __restrict__ gp,
   const float K = (float)(fac[ik1] + (ik2 >= 0 ? fac[ik2] : 0.0));
   const float g = fmaf(D, gx[i], gp[i]);
   gp[i] = g;
-  v[i] = K * g;
+  if (v) v[i] = K * g;
 }
 
 __global__ void k_scale_copy(const float* __restrict__ src, float* __restrict__ dst, size_t n,

@@ -706,38 +706,34 @@ static int force_adj_impl(fpm_plan* p, const float* gF, float* g_rho, cudaStream
   return FPM_OK;
 }
 
-// gx += J_f(x)^T v at the positions x whose paint (buckets) and force
-// meshes (p->F, interleaved when p->f4) are current; uses p->rho as scratch.
 // The next reverse step's drift and kick transposes, when the transposed
-// gather can apply them on the fly (dk_idr >= 0).
+// gather can apply them on the fly (idr >= 0).
 struct NextDriftKick {
   int idr = -1, ik1 = -1, ik2 = -1;
 };
 
-// gx += J^T v at positions x (paint, force and readout transposes).  With
-// vmax_ready the vector paint takes max |v| from p->vmax.  Returns (in
-// *fused) whether the gather also applied `next` to (gx, gp) and left v
-// and max |v| for the next step.
-static int force_jt_impl(fpm_plan* p, const PaintCtx& c, const float* x, float* v, float* gx, const float* F,
-                         cudaStream_t s, bool vmax_ready = false, NextDriftKick next = {}, float* gp = nullptr,
+// gx += J^T v at positions x (paint, force and readout transposes), v_i =
+// K v[i] with K from vk.  With vmax_ready the vector paint takes max |v|
+// from p->vmax.  With `next` (and v = the momentum cotangents gp) the gather
+// then applies next's drift and kick transposes to (gx, gp) and leaves
+// max |K' gp| for the next step; *fused tells whether it did.
+static int force_jt_impl(fpm_plan* p, const PaintCtx& c, const float* x, float* v, KScale vk, float* gx,
+                         const float* F, cudaStream_t s, bool vmax_ready = false, NextDriftKick next = {},
                          bool* fused = nullptr) {
   if (fused) *fused = false;
   FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s,
-                [&] { return launch_paint_vec(c, x, v, p->vmax, p->gF, s, vmax_ready); }));
+                [&] { return launch_paint_vec(c, x, v, vk, p->vmax, p->gF, s, vmax_ready); }));
   FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
-  if (next.idr >= 0 && gp && fused) {
-    const int r = timed(p, FPM_K_READOUT, 1, s, [&] {
-      return launch_gather_adj_dk(c, x, p->rho, F, p->f4, v, gx, gp, p->d_fac, next.idr, next.ik1, next.ik2,
+  if (next.idr >= 0 && fused) {
+    FPM_TRY(timed(p, FPM_K_READOUT, 1, s, [&] {
+      return launch_gather_adj_dk(c, x, p->rho, F, p->f4, v, vk, gx, p->d_fac, next.idr, next.ik1, next.ik2,
                                   p->vmax, s);
-    });
-    if (r == FPM_OK) {
-      *fused = true;
-      return FPM_OK;
-    }
-    if (r != FPM_ENOTIMPL) return r;
+    }));
+    *fused = true;
+    return FPM_OK;
   }
   return timed(p, FPM_K_READOUT, 1, s,
-               [&] { return launch_gather_adj(c, x, p->rho, F, p->f4, v, gx, true, s); });
+               [&] { return launch_gather_adj(c, x, p->rho, F, p->f4, v, gx, true, s, vk); });
 }
 
 extern "C" {
@@ -792,7 +788,8 @@ int fpm_readout_adj(fpm_plan* p, const float* F, const float* dx, const float* g
   FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, dx, s); }));
   FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
   FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
-  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s, [&] { return launch_paint_vec(c, dx, g_f, p->vmax, g_F, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s,
+                [&] { return launch_paint_vec(c, dx, g_f, KScale{}, p->vmax, g_F, s); }));
   return timed(p, FPM_K_READOUT, 1, s,
                [&] { return launch_gather_adj(c, dx, nullptr, F, false, g_f, g_dx, false, s); });
 }
@@ -849,23 +846,45 @@ int fpm_kdk_adj(fpm_plan* p, const float* ckpt, const float* fckpt, const double
     d.ik2 = k > 0 ? 3 * (k - 1) + 2 : -1;
     return d;
   };
-  bool ready = false;   // v = vbuf and max |v| of the next step already applied by the last gather
+  auto kick_of = [&](const NextDriftKick& d) {
+    KScale k;
+    k.fac = p->d_fac;
+    k.ik1 = d.ik1;
+    k.ik2 = d.ik2;
+    return k;
+  };
+  // On brick lattices the velocity cotangents v = K gp are never stored:
+  // the vector paint and the gather scale gp as they read it, and each
+  // gather applies the next step's drift and kick transposes (chain).
+  // Elsewhere v is materialised in vbuf by the drift-kick kernel.
+  const bool chain = kdk_brick_fits(p->pc, p->f4);
+  bool ready = false;   // the last gather applied this step's drift-kick transposes and max |v|
   if (g_p_in) {   // closing half kick at a_n: gx += J^T(x_n) (K gp)
     const float* xn = ckpt + (size_t)nsteps * N3;
+    KScale kn;
+    kn.fac = p->d_fac;
+    kn.ik1 = 3 * (nsteps - 1) + 2;
     FPM_TRY(prepare(nsteps, xn));
-    FPM_TRY(launch_scale_copy(gp, p->vbuf, N3, p->d_fac, 3 * (nsteps - 1) + 2, s));
-    FPM_TRY(force_jt_impl(p, Ck, xn, p->vbuf, g_dx, Fk, s, false, drift_kick(nsteps - 1), gp, &ready));
+    if (chain) {
+      FPM_TRY(force_jt_impl(p, Ck, xn, gp, kn, g_dx, Fk, s, false, drift_kick(nsteps - 1), &ready));
+    } else {
+      FPM_TRY(launch_scale_copy(gp, p->vbuf, N3, p->d_fac, kn.ik1, s));
+      FPM_TRY(force_jt_impl(p, Ck, xn, p->vbuf, KScale{}, g_dx, Fk, s));
+    }
   }
   for (int k = nsteps - 1; k >= 0; --k) {
     const float* xk = ckpt + (size_t)k * N3;
-    if (!ready) {
-      const NextDriftKick d = drift_kick(k);
-      FPM_TRY(launch_adj_drift_kick(g_dx, gp, p->vbuf, N3, p->d_fac, d.idr, d.ik1, d.ik2, s));
-    }
+    const NextDriftKick d = drift_kick(k);
+    if (!ready)
+      FPM_TRY(launch_adj_drift_kick(g_dx, gp, chain ? nullptr : p->vbuf, N3, p->d_fac, d.idr, d.ik1, d.ik2, s));
     FPM_TRY(prepare(k, xk));
-    const bool vmax_ready = ready;
-    FPM_TRY(force_jt_impl(p, Ck, xk, p->vbuf, g_dx, Fk, s, vmax_ready, k > 0 ? drift_kick(k - 1) : NextDriftKick{},
-                          gp, &ready));
+    if (chain) {
+      const bool vmax_ready = ready;
+      FPM_TRY(force_jt_impl(p, Ck, xk, gp, kick_of(d), g_dx, Fk, s, vmax_ready,
+                            k > 0 ? drift_kick(k - 1) : NextDriftKick{}, &ready));
+    } else {
+      FPM_TRY(force_jt_impl(p, Ck, xk, p->vbuf, KScale{}, g_dx, Fk, s));
+    }
   }
   g_launches += 1 + 2 * nsteps;
   return FPM_OK;

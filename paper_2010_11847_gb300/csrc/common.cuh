@@ -65,6 +65,16 @@ inline FastDiv make_fastdiv(uint32_t d) {
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return __umulhi(n, f.m) >> f.sh; }
 
+// A kick factor read from the FP64 factor table on the device: fac[ik1]
+// (+ fac[ik2] when ik2 >= 0), rounded once to float; 1 when fac is null.
+struct KScale {
+  const double* fac = nullptr;
+  int ik1 = -1, ik2 = -1;
+};
+__device__ __forceinline__ float kscale(const KScale& k) {
+  return k.fac ? (float)(k.fac[k.ik1] + (k.ik2 >= 0 ? k.fac[k.ik2] : 0.0)) : 1.f;
+}
+
 // Geometry constants handed to kernels.
 struct Geom {
   int np;          // particles per side

@@ -119,17 +119,21 @@ int launch_kdk_brick(const PaintCtx& c, const float* dx, float* dx_out, float* p
                      int ik1, int ik2, int idr, uint32_t* keys, cudaStream_t s);
 
 // paint.cu: adjoints at fixed positions
+// v_i = K v[i] with K from vk (scaled v needs the brick gather: FPM_EINVAL elsewhere)
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
-                      const float* v, float* g_dx, bool accumulate, cudaStream_t s);
-// vmax_ready: *vmax already holds max |v| (bit pattern), e.g. from launch_gather_adj_dk
-int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
+                      const float* v, float* g_dx, bool accumulate, cudaStream_t s, KScale vk = KScale{});
+// The three channels v_i = K v[ch][i] (K from vk); vmax_ready: *vmax
+// already holds max |K v| (bit pattern), e.g. from launch_gather_adj_dk.
+int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, KScale vk, unsigned* vmax, float* out,
                      cudaStream_t s, bool vmax_ready = false);
-// launch_gather_adj (accumulating, float4 force, brick lattices) followed per
-// particle by the next reverse step's drift and kick transposes (gp += D
-// g_dx, v = K gp in place) and max |v| into *vmax; FPM_ENOTIMPL where the
-// lattice or layout has no brick gather (the caller then runs them apart).
-int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* v,
-                         float* g_dx, float* gp, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
+// launch_gather_adj (accumulating, float4 force, brick lattices) with the
+// cotangent velocities v = K gp taken from the momentum cotangents gp (K
+// from vk), followed per particle by the next reverse step's drift and kick
+// transposes (gp += D g_dx in place, K' from fac[ik1] (+ fac[ik2])) and
+// max |K' gp| into *vmax; FPM_ENOTIMPL where the lattice or layout has no
+// brick gather (the caller then runs them apart).
+int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* gp,
+                         KScale vk, float* g_dx, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
                          cudaStream_t s);
 
 // adjoint.cu: spectral adjoints (power-of-two sizes) and elementwise steps

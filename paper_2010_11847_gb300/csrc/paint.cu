@@ -422,9 +422,12 @@ __global__ void __launch_bounds__(256) k_gather_adj(const float* __restrict__ dx
 // With a drift-kick tail (dk.gp non-null) each particle then applies the
 // next reverse step's drift and kick transposes to its new cotangent, as
 // k_adj_drift_kick does (gp += D g_dx; v = K gp, v overwritten in place),
-// and the block records max |v| for the next vector paint.
+// and the block records max |v| for the next vector paint.  In this form
+// the cotangent velocities are not stored: v holds the momentum cotangents
+// gp themselves, the kernel takes v_i = K gp_i with the current kick factor
+// (vk), updates gp in place and records max |K' gp'| for the next step.
 struct DriftKickTail {
-  float* gp = nullptr;
+  bool on = false;
   const double* fac = nullptr;
   int idr = -1, ik1 = -1, ik2 = -1;
   unsigned* vmax = nullptr;        // zeroed by the launcher
@@ -433,14 +436,14 @@ struct DriftKickTail {
 template <bool F4>
 __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __restrict__ dx, Geom g, size_t N,
                                                                  size_t M, const float* __restrict__ g_rho,
-                                                                 const float* __restrict__ F,
-                                                                 float* __restrict__ v,
+                                                                 const float* __restrict__ F, float* v, KScale vk,
                                                                  float* __restrict__ g_dx, int accumulate,
                                                                  DriftKickTail dk) {
   using BS = KdkBrick;
   __shared__ unsigned s_max[KB_THREADS / 32];
+  const float Kc = kscale(vk);
   float Dn = 0.f, Kn = 0.f;
-  if (dk.gp) {
+  if (dk.on) {
     Dn = (float)dk.fac[dk.idr];
     Kn = (float)(dk.fac[dk.ik1] + (dk.ik2 >= 0 ? dk.fac[dk.ik2] : 0.0));
   }
@@ -461,7 +464,8 @@ __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __
 #pragma unroll 1
   for (int it = 0; it < BS::ITERS; ++it) {
     const uint32_t i = brick_particle<BS>(it, bx, by, bz, np);
-    const float d[3] = {dn[0], dn[1], dn[2]}, vi[3] = {vn[0], vn[1], vn[2]};
+    const float d[3] = {dn[0], dn[1], dn[2]}, vr[3] = {vn[0], vn[1], vn[2]};
+    const float vi[3] = {Kc * vr[0], Kc * vr[1], Kc * vr[2]};
     if (it + 1 < BS::ITERS) {
       const uint32_t inext = brick_particle<BS>(it + 1, bx, by, bz, np);
 #pragma unroll
@@ -500,16 +504,14 @@ __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __
     for (int a = 0; a < 3; ++a) {
       const float gx = accumulate ? __ldcs(g_dx + a * N + i) + gsum[a] : gsum[a];
       __stcs(g_dx + a * N + i, gx);
-      if (dk.gp) {
-        const float gq = fmaf(Dn, gx, __ldcs(dk.gp + a * N + i));
-        __stcs(dk.gp + a * N + i, gq);
-        const float vq = Kn * gq;
-        __stcs(v + a * N + i, vq);
-        vm = max(vm, __float_as_uint(fabsf(vq)));
+      if (dk.on) {
+        const float gq = fmaf(Dn, gx, vr[a]);
+        __stcs(v + a * N + i, gq);
+        vm = max(vm, __float_as_uint(fabsf(Kn * gq)));
       }
     }
   }
-  if (dk.gp) {
+  if (dk.on) {
     for (int off = 16; off; off >>= 1) vm = max(vm, __shfl_xor_sync(0xffffffffu, vm, off));
     if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = vm;
     __syncthreads();
@@ -523,10 +525,11 @@ __global__ void __launch_bounds__(KB_THREADS) k_gather_adj_brick(const float* __
 
 // max |v| over n values as the bit pattern of a non-negative float (the
 // integer order of such patterns is their numeric order): order-independent.
-__global__ void k_maxabs(const float* __restrict__ v, size_t n, unsigned* __restrict__ out) {
+__global__ void k_maxabs(const float* __restrict__ v, KScale vk, size_t n, unsigned* __restrict__ out) {
+  const float K = kscale(vk);
   unsigned m = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    m = max(m, __float_as_uint(fabsf(v[i])));
+    m = max(m, __float_as_uint(fabsf(K * v[i])));
   for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
@@ -561,11 +564,12 @@ __device__ __forceinline__ void body_halo_vec(const unsigned long long* __restri
 }
 
 // Readout transpose for one channel: out_c = sum_i W(x_i - c) v_i (no
-// mass), deterministic signed fixed point in units set by max |v|.
+// mass), v_i = K vch_i (vk), deterministic signed fixed point in units set
+// by max |v|.
 __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restrict__ dx, size_t N,
                                                           const uint32_t* __restrict__ items,
                                                           const uint32_t* __restrict__ tile_start, Geom g,
-                                                          const float* __restrict__ vch,
+                                                          const float* __restrict__ vch, KScale vk,
                                                           const unsigned* __restrict__ vmax,
                                                           float* __restrict__ out,
                                                           unsigned long long* __restrict__ halo,
@@ -578,6 +582,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
   const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
   const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
   const float scale = signed_scale(*vmax), inv = 1.f / scale;
+  const float K = kscale(vk);
   for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
   __syncthreads();
   for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
     } else if (!particle_local<false>(dx, N, i, g, o, l, t)) {
       continue;
     }
-    const float vs = __ldg(vch + i) * scale;
+    const float vs = (K * __ldg(vch + i)) * scale;
     const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
 #pragma unroll
@@ -647,16 +652,20 @@ __global__ void __launch_bounds__(768) k_halo_vec(const unsigned long long* __re
 }
 
 int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4,
-                      const float* v, float* g_dx, bool accumulate, cudaStream_t s) {
+                      const float* v, float* g_dx, bool accumulate, cudaStream_t s, KScale vk) {
   const int it = readout_iters(c.N);
   if (KDK_BRICK && KdkBrick::fits(c.g.np)) {
     float* vv = const_cast<float*>(v);     // read only without a drift-kick tail
     if (f4)
-      k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, vv, g_dx,
-                                                                              accumulate, DriftKickTail{});
+      k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, vv,
+                                                                              vk, g_dx, accumulate,
+                                                                              DriftKickTail{});
     else
       k_gather_adj_brick<false><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, vv,
-                                                                               g_dx, accumulate, DriftKickTail{});
+                                                                               vk, g_dx, accumulate,
+                                                                               DriftKickTail{});
+  } else if (vk.fac) {
+    return FPM_EINVAL;     // scaled cotangents need the brick gather
   } else if (f4)
     k_gather_adj<true><<<grid_of(c.N, 256 * it), 256, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, accumulate, it);
   else
@@ -668,33 +677,33 @@ int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, co
 
 // Readout transpose of the 3 channels of v into meshes out[3][M]; the tile
 // buckets must hold the positions dx (a paint of dx ran last on this ctx).
-int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* v,
-                         float* g_dx, float* gp, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
+int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho, const float* F, bool f4, float* gp,
+                         KScale vk, float* g_dx, const double* fac, int idr, int ik1, int ik2, unsigned* vmax,
                          cudaStream_t s) {
   if (!(KDK_BRICK && KdkBrick::fits(c.g.np) && f4)) return FPM_ENOTIMPL;
   FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
   DriftKickTail dk;
-  dk.gp = gp;
+  dk.on = true;
   dk.fac = fac;
   dk.idr = idr;
   dk.ik1 = ik1;
   dk.ik2 = ik2;
   dk.vmax = vmax;
-  k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, v, g_dx, 1,
-                                                                          dk);
+  k_gather_adj_brick<true><<<KdkBrick::blocks(c.g.np), KB_THREADS, 0, s>>>(dx, c.g, c.N, c.M, g_rho, F, gp, vk, g_dx,
+                                                                          1, dk);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }
 
-int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, unsigned* vmax, float* out,
+int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, KScale vk, unsigned* vmax, float* out,
                      cudaStream_t s, bool vmax_ready) {
   if (!vmax_ready) {
     FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
-    k_maxabs<<<1024, 256, 0, s>>>(v, 3 * c.N, vmax);
+    k_maxabs<<<1024, 256, 0, s>>>(v, vk, 3 * c.N, vmax);
     FPM_CUDA_TRY(cudaGetLastError());
   }
   for (int ch = 0; ch < 3; ++ch) {
-    k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vmax,
+    k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vk, vmax,
                                                 out + ch * c.M, c.halo, cells_of(c), c.tile_done);
     FPM_CUDA_TRY(cudaGetLastError());
     if (!c.tile_done) {
