@@ -585,30 +585,48 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
   const float K = kscale(vk);
   for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
   __syncthreads();
-  for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-    const uint32_t i = __ldg(items + k);
-    int l[3];
-    float t[3];
-    if (cells) {
-      const uint32_t lc = __ldg(cells + k);
-      l[0] = (int)(lc >> 8);
-      l[1] = (int)(lc >> 4) & (TILE - 1);
-      l[2] = (int)lc & (TILE - 1);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float d = __ldg(dx + a * N + i);
-        t[a] = d - floorf(d);
-      }
-    } else if (!particle_local<false>(dx, N, i, g, o, l, t)) {
-      continue;
-    }
-    const float vs = (K * __ldg(vch + i)) * scale;
+  auto deposit = [&](const int* l, const float* t, float v) {
+    const float vs = (K * v) * scale;
     const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
 #pragma unroll
     for (int c = 0; c < 8; ++c)
       acc_add_signed(lo, hi, base + (c >> 2) * TILE1 * TILE1 + ((c >> 1) & 1) * TILE1 + (c & 1),
                      __float2int_rn(wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1] * vs));
+  };
+  if (cells) {
+    // two particles per thread and pass, their loads in flight together
+    const uint32_t B = blockDim.x;
+    for (uint32_t k0 = s0 + threadIdx.x; k0 < s1; k0 += 2 * B) {
+      const bool a1 = k0 + B < s1;
+      const uint32_t i0 = __ldg(items + k0), i1 = a1 ? __ldg(items + k0 + B) : 0u;
+      const uint32_t c0 = __ldg(cells + k0), c1 = a1 ? __ldg(cells + k0 + B) : 0u;
+      float d0[3], d1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        d0[a] = __ldg(dx + a * N + i0);
+        if (a1) d1[a] = __ldg(dx + a * N + i1);
+      }
+      const float v0 = __ldg(vch + i0), v1 = a1 ? __ldg(vch + i1) : 0.f;
+      {
+        const int l[3] = {(int)(c0 >> 8), (int)(c0 >> 4) & (TILE - 1), (int)c0 & (TILE - 1)};
+        const float t[3] = {d0[0] - floorf(d0[0]), d0[1] - floorf(d0[1]), d0[2] - floorf(d0[2])};
+        deposit(l, t, v0);
+      }
+      if (a1) {
+        const int l[3] = {(int)(c1 >> 8), (int)(c1 >> 4) & (TILE - 1), (int)c1 & (TILE - 1)};
+        const float t[3] = {d1[0] - floorf(d1[0]), d1[1] - floorf(d1[1]), d1[2] - floorf(d1[2])};
+        deposit(l, t, v1);
+      }
+    }
+  } else {
+    for (uint32_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+      const uint32_t i = __ldg(items + k);
+      int l[3];
+      float t[3];
+      if (!particle_local<false>(dx, N, i, g, o, l, t)) continue;
+      deposit(l, t, __ldg(vch + i));
+    }
   }
   __syncthreads();
   paint_writeout_conv(Acc32{lo, hi}, o, tile, g, out, halo,

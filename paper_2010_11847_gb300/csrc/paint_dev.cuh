@@ -425,28 +425,39 @@ __device__ __forceinline__ void body_paint_bucket_acc(const float* __restrict__ 
   __syncthreads();
   bool bad = false;
   const int nw = (n + 31) & ~31;
-  for (int k = threadIdx.x; k < nw; k += blockDim.x) {
-    const bool active = k < n;
-    int l[3] = {0, 0, 0};
-    float t[3] = {0.f, 0.f, 0.f};
-    if (active) {
-      const uint32_t i = ld_part<COH>(items + s0 + k);
-      if (cells) {
-        // in-tile cell from the bucketing (the key's low 3 log2 TE bits), fraction from dx
-        const uint32_t lc = ld_part<COH>(cells + s0 + k);
-        l[0] = (int)(lc >> (2 * C::LG));
-        l[1] = (int)(lc >> C::LG) & (TE - 1);
-        l[2] = (int)lc & (TE - 1);
+  if (cells) {
+    // two particles per thread and pass: both items' loads, then both
+    // particles' dx gathers, are in flight together
+    for (int k0 = threadIdx.x; k0 < nw; k0 += 2 * blockDim.x) {
+      const int k1 = k0 + blockDim.x;          // k1 < nw is uniform over the warp
+      const bool a0 = k0 < n, a1 = k1 < n;
+      const uint32_t i0 = a0 ? ld_part<COH>(items + s0 + k0) : 0u, i1 = a1 ? ld_part<COH>(items + s0 + k1) : 0u;
+      const uint32_t c0 = a0 ? ld_part<COH>(cells + s0 + k0) : 0u, c1 = a1 ? ld_part<COH>(cells + s0 + k1) : 0u;
+      float d0[3] = {0.f, 0.f, 0.f}, d1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float d = ld_part<COH>(dx + a * N + i);
-          t[a] = d - floorf(d);
-        }
-      } else {
-        bad |= !particle_local<COH, TE>(dx, N, i, g, o, l, t);
+      for (int a = 0; a < 3; ++a) {
+        if (a0) d0[a] = ld_part<COH>(dx + a * N + i0);
+        if (a1) d1[a] = ld_part<COH>(dx + a * N + i1);
+      }
+      {
+        const int l[3] = {(int)(c0 >> (2 * C::LG)), (int)(c0 >> C::LG) & (TE - 1), (int)c0 & (TE - 1)};
+        const float t[3] = {d0[0] - floorf(d0[0]), d0[1] - floorf(d0[1]), d0[2] - floorf(d0[2])};
+        deposit_warp<A, TE>(acc, a0, l, t);
+      }
+      if (k1 < nw) {
+        const int l[3] = {(int)(c1 >> (2 * C::LG)), (int)(c1 >> C::LG) & (TE - 1), (int)c1 & (TE - 1)};
+        const float t[3] = {d1[0] - floorf(d1[0]), d1[1] - floorf(d1[1]), d1[2] - floorf(d1[2])};
+        deposit_warp<A, TE>(acc, a1, l, t);
       }
     }
-    deposit_warp<A, TE>(acc, active, l, t);
+  } else {
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) {
+      const bool active = k < n;
+      int l[3] = {0, 0, 0};
+      float t[3] = {0.f, 0.f, 0.f};
+      if (active) bad |= !particle_local<COH, TE>(dx, N, ld_part<COH>(items + s0 + k), g, o, l, t);
+      deposit_warp<A, TE>(acc, active, l, t);
+    }
   }
   if (bad) atomicOr(err, ERR_RANGE);
   __syncthreads();
