@@ -406,10 +406,12 @@ __global__ void __launch_bounds__(RegCfg<N>::THREADS, 1024 / RegCfg<N>::THREADS)
 // F_d(c) = [8 (phi(c + e_d) - phi(c - e_d)) - (phi(c + 2 e_d) - phi(c - 2 e_d))] / 12,
 // whose Fourier symbol is i (8 sin w - sin 2w) / 6 = i g(w) of Eq. 5 (zero
 // at the Nyquist frequency by itself).  A block owns a TZ x TY patch of a
-// y-z plane and marches through XC planes of x, keeping a ring of five
-// halo-padded planes in shared memory; the next plane is fetched into
-// registers while the current one is differenced.
+// y-z plane and marches through XC planes of x, keeping a ring of RING
+// halo-padded planes in shared memory; each plane is fetched by per-thread
+// asynchronous copies PF planes ahead of its first use (one commit group
+// per plane), so that several planes' loads are in flight per block.
 constexpr int ST_XC = 32;                  // x planes per block
+constexpr int ST_PF = 3;                   // planes fetched ahead
 template <int N>
 struct StCfg {
   static constexpr int TZ = N < 32 ? N : 32;
@@ -417,51 +419,57 @@ struct StCfg {
   static constexpr int PZ = TZ + 4, PY = TY + 4, PLANE = PZ * PY;
   static constexpr int XC = N < ST_XC ? N : ST_XC;
   static constexpr int LOADS = (PLANE + 255) / 256;
+  static constexpr int RING = 6 + ST_PF;   // 5 planes in use, PF in flight, 1 being refilled
+  static constexpr size_t SMEM = (size_t)RING * PLANE * sizeof(float);
 };
 
 __device__ __forceinline__ float fd4(float m2, float m1, float p1, float p2) {
   return fmaf(0.6666666666666666f, p1 - m1, -0.08333333333333333f * (p2 - m2));
 }
 
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
+// ring: RING * PLANE floats of shared memory (4-byte aligned).
 template <int N, bool F4>
 __device__ __forceinline__ void body_stencil(const float* __restrict__ phi, float* __restrict__ F, size_t M,
                                              float* ring, int bz, int by, int bx) {
   using C = StCfg<N>;
-  constexpr int TZ = C::TZ, TY = C::TY, PZ = C::PZ, PLANE = C::PLANE, XC = C::XC;
+  constexpr int TZ = C::TZ, TY = C::TY, PZ = C::PZ, PLANE = C::PLANE, XC = C::XC, RING = C::RING;
   const int z0 = bz * TZ, y0 = by * TY, x0 = bx * XC;
   const int tz = threadIdx.x % TZ, ty = threadIdx.x / TZ;
-  float pre[C::LOADS];
-  auto fetch = [&](int x) {
-    const float* pl = phi + (size_t)(x & (N - 1)) * N * N;
+  // plane q (x = x0 - 2 + q, q = 0 .. XC + 3) goes to slot q % RING; one
+  // commit group per call, empty past the last plane, so that the count of
+  // groups in flight after plane q is always ST_PF
+  auto fetch = [&](int q) {
+    if (q < XC + 4) {
+      const float* pl = phi + (size_t)((x0 - 2 + q) & (N - 1)) * N * N;
+      float* dst = ring + (q % RING) * PLANE;
 #pragma unroll
-    for (int k = 0; k < C::LOADS; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      if (e < PLANE) {
-        const int r = e / PZ, c = e - r * PZ;
-        pre[k] = __ldcg(pl + (size_t)((y0 - 2 + r) & (N - 1)) * N + ((z0 - 2 + c) & (N - 1)));
+      for (int k = 0; k < C::LOADS; ++k) {
+        const int e = threadIdx.x + 256 * k;
+        if (e < PLANE) {
+          const int r = e / PZ, c = e - r * PZ;
+          cp_async4(dst + e, pl + (size_t)((y0 - 2 + r) & (N - 1)) * N + ((z0 - 2 + c) & (N - 1)));
+        }
       }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  auto stash = [&](int slot) {
-#pragma unroll
-    for (int k = 0; k < C::LOADS; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      if (e < PLANE) ring[slot * PLANE + e] = pre[k];
-    }
-  };
-  for (int j = 0; j < 4; ++j) {            // planes x0-2 .. x0+1
-    fetch(x0 - 2 + j);
-    stash(j);
-  }
-  fetch(x0 + 2);
+  for (int q = 0; q < 5 + ST_PF; ++q) fetch(q);
   const int cidx = (ty + 2) * PZ + tz + 2;
   for (int j = 0; j < XC; ++j) {
-    stash((j + 4) % 5);
+    // planes j .. j+4 complete (ST_PF later groups may still be in flight),
+    // visible to the block, and slot (j + 5 + ST_PF) % RING (plane j - 1,
+    // last read in iteration j - 1) free for refilling
+    asm volatile("cp.async.wait_group %0;" ::"n"(ST_PF) : "memory");
     __syncthreads();
-    if (j + 1 < XC) fetch(x0 + j + 3);
-    const float* c = ring + ((j + 2) % 5) * PLANE;
-    const float fx = fd4(ring[(j % 5) * PLANE + cidx], ring[((j + 1) % 5) * PLANE + cidx],
-                         ring[((j + 3) % 5) * PLANE + cidx], ring[((j + 4) % 5) * PLANE + cidx]);
+    fetch(j + 5 + ST_PF);
+    const float* c = ring + ((j + 2) % RING) * PLANE;
+    const float fx = fd4(ring[(j % RING) * PLANE + cidx], ring[((j + 1) % RING) * PLANE + cidx],
+                         ring[((j + 3) % RING) * PLANE + cidx], ring[((j + 4) % RING) * PLANE + cidx]);
     const float fy = fd4(c[cidx - 2 * PZ], c[cidx - PZ], c[cidx + PZ], c[cidx + 2 * PZ]);
     const float fz = fd4(c[cidx - 2], c[cidx - 1], c[cidx + 1], c[cidx + 2]);
     const size_t o = ((size_t)(x0 + j) * N + (y0 + ty)) * N + z0 + tz;
@@ -472,8 +480,9 @@ __device__ __forceinline__ void body_stencil(const float* __restrict__ phi, floa
       F[M + o] = fy;
       F[2 * M + o] = fz;
     }
-    __syncthreads();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();                         // the ring may be reused after return
 }
 
 // Transpose of the gradient: out = -sum_d D_d g_d for g = [3][N^3] (D is
@@ -502,7 +511,7 @@ __global__ void __launch_bounds__(256) k_div_neg(const float* __restrict__ g, fl
 
 template <int N, bool F4>
 __global__ void __launch_bounds__(256) k_stencil(const float* __restrict__ phi, float* __restrict__ F, size_t M) {
-  __shared__ float ring[5 * StCfg<N>::PLANE];
+  __shared__ float ring[StCfg<N>::RING * StCfg<N>::PLANE];
   body_stencil<N, F4>(phi, F, M, ring, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
