@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(BT, 3) k_batch_step(BatchArgs a) {
         }
         case PH_SCAN: body_scan_tiles(d.tile_count, d.ntiles, d.tile_start, d.tile_cursor, su, 1); break;
         case PH_SCATTER:
-          if (d.te == 8) body_scatter_cube<BT, 8>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su);
-          else body_scatter_cube<BT, 16>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su);
+          if (d.te == 8) body_scatter_cube<BT, 8>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su, d.err);
+          else body_scatter_cube<BT, 16>(d.keys, d.g.np, d.tile_cursor, d.items, d.cells, local, su, d.err);
           break;
         case PH_PAINT:
           if (d.te == 8)

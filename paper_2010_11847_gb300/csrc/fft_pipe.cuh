@@ -198,8 +198,9 @@ __device__ __forceinline__ void comp_zf(float2* spec, size_t r0, float2* buf, co
   __syncthreads();                       // the exchange area overlaps other lines' rows
   float2* lb = buf + g * RL;
   RegFft<N, P::V>::template run<false, 1>(v, lb, t, tw, 1 + g);
+  const int st = sw16(t);                        // t < T: sw16(t + T s) = sw16(t) ^ sw16(T s)
 #pragma unroll
-  for (int s = 0; s < P::V; ++s) lb[sw16(t + T * s)] = v[s];
+  for (int s = 0; s < P::V; ++s) lb[st ^ sw16(T * s)] = v[s];
   __syncthreads();
   const size_t x = r0 / N, y0 = r0 - x * N;
   for (int idx = threadIdx.x; idx < NH * L; idx += P::THREADS) {
@@ -246,8 +247,9 @@ __device__ __forceinline__ void comp_zi(float* phi, size_t r0, float2* buf, cons
   const int g = threadIdx.x / T, t = threadIdx.x - g * T;
   float2* lb = buf + g * RL;
   float2 v[P::V];
+  const int st = sw16(t);
 #pragma unroll
-  for (int s = 0; s < P::V; ++s) v[s] = lb[sw16(t + T * s)];
+  for (int s = 0; s < P::V; ++s) v[s] = lb[st ^ sw16(T * s)];
   xsync<T>(1 + g);
   RegFft<N, P::V>::template run<true, 1>(v, lb, t, tw, 1 + g);
   float* dst = phi + (r0 + 2 * g) * N;

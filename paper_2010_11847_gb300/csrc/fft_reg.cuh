@@ -23,13 +23,17 @@
 
 namespace fpm {
 
-__device__ __forceinline__ int rp(int i) { return i + (i >> 3); }   // padded exchange index
+__host__ __device__ __forceinline__ constexpr int rp(int i) { return i + (i >> 3); }   // padded exchange index
 // Exchange index of a line: padded (LAY 0, line stride rline), or XOR-swizzled
 // within 16-element rows (LAY 1, line stride N + 2).  The swizzle makes both
 // the Stockham writes and the contiguous read-back free of bank conflicts
 // when a line's threads are consecutive lanes; the padding suits lines that
 // are interleaved across lanes (the x pass).
-__device__ __forceinline__ int sw16(int i) { return i ^ (((i >> 4) & 7) | ((i >> 3) & 8)); }
+// sw16 is linear over XOR (each bit of the mask it XORs in is one input
+// bit), so for indices made of disjoint bit fields, e.g. t + T*s with t < T
+// a power of two, sw16(a + b) = sw16(a) ^ sw16(b): the run-time part is
+// swizzled once and each compile-time part costs one XOR.
+__host__ __device__ __forceinline__ constexpr int sw16(int i) { return i ^ (((i >> 4) & 7) | ((i >> 3) & 8)); }
 template <int LAY>
 __device__ __forceinline__ int xidx(int i) { return LAY == 0 ? rp(i) : sw16(i); }
 template <int N>
@@ -72,15 +76,27 @@ __device__ __forceinline__ void reg_stage(float2 (&v)[V], float2* buf, int t, co
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q + Q * r] = x[r];
     } else {
-      const int base = (j / NS) * NS * R + k;
+      const int base = (j / NS) * NS * R + k;     // zero in the bits of r * NS
+      if (LAY == 1) {
+        const int sb = sw16(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[xidx<LAY>(base + r * NS)] = x[r];
+        for (int r = 0; r < R; ++r) buf[sb ^ sw16(r * NS)] = x[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[xidx<LAY>(base + r * NS)] = x[r];
+      }
     }
   }
   if (!LAST) {
     xsync<T>(sid);
+    if (LAY == 1) {
+      const int st = sw16(t);                    // t < T
 #pragma unroll
-    for (int s = 0; s < V; ++s) v[s] = buf[xidx<LAY>(t + T * s)];
+      for (int s = 0; s < V; ++s) v[s] = buf[st ^ sw16(T * s)];
+    } else {
+#pragma unroll
+      for (int s = 0; s < V; ++s) v[s] = buf[xidx<LAY>(t + T * s)];
+    }
     xsync<T>(sid);
   }
 }

@@ -55,9 +55,10 @@ inline uint16_t* cells_of(const PaintCtx& c) { return PAINT_CELLS ? c.cells : nu
 __global__ void __launch_bounds__(SC_THREADS, 4) k_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                              uint32_t* __restrict__ cursor,
                                                              uint32_t* __restrict__ items,
-                                                             uint16_t* __restrict__ cells) {
+                                                             uint16_t* __restrict__ cells,
+                                                             int* __restrict__ err) {
   __shared__ uint32_t tbl[3 * SC_TBL];
-  body_scatter_cube<SC_THREADS>(keys, np, cursor, items, cells, blockIdx.x, tbl);
+  body_scatter_cube<SC_THREADS>(keys, np, cursor, items, cells, blockIdx.x, tbl, err);
 }
 
 __global__ void __launch_bounds__(PB_THREADS) k_paint_bucket(const float* __restrict__ dx, size_t N,
@@ -284,7 +285,7 @@ int launch_scan(const PaintCtx& c, cudaStream_t s) {
 int launch_scatter(const PaintCtx& c, cudaStream_t s) {
   if (c.g.np % SC_CUBE != 0) return FPM_EINVAL;   // every supported lattice size is a multiple of 16
   k_scatter_cube<<<scatter_cube_items(c.g.np, SC_THREADS), SC_THREADS, 0, s>>>(c.keys, c.g.np, c.tile_cursor,
-                                                                             c.items, cells_of(c));
+                                                                             c.items, cells_of(c), c.err);
   FPM_CUDA_TRY(cudaGetLastError());
   return FPM_OK;
 }

@@ -135,10 +135,14 @@ __host__ __device__ inline int scatter_cube_items(int np, int threads) {
   return (np / cx) * (np / SC_CUBE) * (np / SC_CUBE);
 }
 
+// A place at or past np^3 (tile counts that do not match the keys, which
+// the callers never produce) is not written: it raises ERR_RANGE instead.
 template <int NT, int TE = 16>
 __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ keys, int np,
                                                   uint32_t* __restrict__ cursor, uint32_t* __restrict__ items,
-                                                  uint16_t* __restrict__ cells, int item, uint32_t* tbl) {
+                                                  uint16_t* __restrict__ cells, int item, uint32_t* tbl,
+                                                  int* __restrict__ err) {
+  const uint32_t nall = (uint32_t)np * np * np;
   uint32_t* t_tile = tbl;
   uint32_t* t_cnt = tbl + SC_TBL;
   uint32_t* t_base = tbl + 2 * SC_TBL;
@@ -183,8 +187,12 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
     sl = __shfl_sync(full, sl, leader);
     const uint32_t place = __shfl_sync(full, off, leader) + __popc(grp & ((1u << lane) - 1u));
     if (sl < 0) {
-      items[place] = index_of(e);
-      if (cells) cells[place] = (uint16_t)(key[e] & (TileC<TE>::E3 - 1));
+      if (place < nall) {
+        items[place] = index_of(e);
+        if (cells) cells[place] = (uint16_t)(key[e] & (TileC<TE>::E3 - 1));
+      } else {
+        atomicOr(err, ERR_RANGE);
+      }
       packed[e] = 0xffffffffu;
     } else {
       packed[e] = ((uint32_t)sl << 16) | place;
@@ -198,6 +206,10 @@ __device__ __forceinline__ void body_scatter_cube(const uint32_t* __restrict__ k
   for (int e = 0; e < SC_PER; ++e)
     if (packed[e] != 0xffffffffu) {
       const uint32_t place = t_base[packed[e] >> 16] + (packed[e] & 0xffffu);
+      if (place >= nall) {
+        atomicOr(err, ERR_RANGE);
+        continue;
+      }
       items[place] = index_of(e);
       if (cells) cells[place] = (uint16_t)(key[e] & (TileC<TE>::E3 - 1));
     }
