@@ -502,27 +502,40 @@ __device__ __forceinline__ void body_stencil(const float* __restrict__ phi, floa
 }
 
 // Transpose of the gradient: out = -sum_d D_d g_d for g = [3][N^3] (D is
-// antisymmetric: D^T = -D).  One cell per thread; the neighbour loads of a
-// warp are coalesced along z and shared through L1.
+// antisymmetric: D^T = -D).  A block owns a TZ x TY patch of y-z columns
+// (the stencil's StCfg) and each thread marches XC planes of x: the x
+// difference comes from a five-plane window of g_x in registers (one new
+// load per cell, fetched a plane ahead), the y and z differences from
+// neighbour loads in the current plane, shared through L1.
 template <int N>
 __global__ void __launch_bounds__(256) k_div_neg(const float* __restrict__ g, float* __restrict__ out) {
+  using C = StCfg<N>;
   constexpr size_t M = (size_t)N * N * N;
-  const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
-  if (i >= M) return;
-  const int z = (int)(i % N), y = (int)((i / N) % N), x = (int)(i / ((size_t)N * N));
+  const int z = blockIdx.x * C::TZ + threadIdx.x % C::TZ, y = blockIdx.y * C::TY + threadIdx.x / C::TZ;
+  const int x0 = blockIdx.z * C::XC;
   auto at = [](int xx, int yy, int zz) {
     return ((size_t)(xx & (N - 1)) * N + (yy & (N - 1))) * N + (zz & (N - 1));
   };
   const float* gx = g;
   const float* gy = g + M;
   const float* gz = g + 2 * M;
-  const float dx_ = fd4(__ldg(gx + at(x - 2, y, z)), __ldg(gx + at(x - 1, y, z)), __ldg(gx + at(x + 1, y, z)),
-                        __ldg(gx + at(x + 2, y, z)));
-  const float dy_ = fd4(__ldg(gy + at(x, y - 2, z)), __ldg(gy + at(x, y - 1, z)), __ldg(gy + at(x, y + 1, z)),
-                        __ldg(gy + at(x, y + 2, z)));
-  const float dz_ = fd4(__ldg(gz + at(x, y, z - 2)), __ldg(gz + at(x, y, z - 1)), __ldg(gz + at(x, y, z + 1)),
-                        __ldg(gz + at(x, y, z + 2)));
-  out[i] = -(dx_ + dy_ + dz_);
+  float w[5];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w[k] = __ldg(gx + at(x0 - 2 + k, y, z));
+  float nxt = __ldg(gx + at(x0 + 2, y, z));
+  for (int j = 0; j < C::XC; ++j) {
+    const int x = x0 + j;
+    w[4] = nxt;
+    if (j + 1 < C::XC) nxt = __ldg(gx + at(x + 3, y, z));
+    const float dx_ = fd4(w[0], w[1], w[3], w[4]);
+    const float dy_ = fd4(__ldg(gy + at(x, y - 2, z)), __ldg(gy + at(x, y - 1, z)), __ldg(gy + at(x, y + 1, z)),
+                          __ldg(gy + at(x, y + 2, z)));
+    const float dz_ = fd4(__ldg(gz + at(x, y, z - 2)), __ldg(gz + at(x, y, z - 1)), __ldg(gz + at(x, y, z + 1)),
+                          __ldg(gz + at(x, y, z + 2)));
+    out[at(x, y, z)] = -(dx_ + dy_ + dz_);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = w[k + 1];
+  }
 }
 
 template <int N, bool F4>

@@ -472,8 +472,8 @@ int fft_pot_inverse(const FftTables& t, float2* spec, float* phi, unsigned* ctr,
 template <int N>
 static int div_impl(const float* g, float* out, cudaStream_t s) {
   if constexpr (is_pow2_size(N)) {
-    const size_t M = (size_t)N * N * N;
-    k_div_neg<N><<<(unsigned)((M + 255) / 256), 256, 0, s>>>(g, out);
+    using C = StCfg<N>;
+    k_div_neg<N><<<dim3(N / C::TZ, N / C::TY, N / C::XC), 256, 0, s>>>(g, out);
     FPM_CUDA_TRY(cudaGetLastError());
     return FPM_OK;
   }
