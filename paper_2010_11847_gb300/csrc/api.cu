@@ -73,6 +73,8 @@ struct fpm_plan {
   float* gF = nullptr;         // 3 meshes (cotangent of the force meshes)
   float* vbuf = nullptr;       // [3][N] kick-weighted momentum cotangent
   unsigned* vmax = nullptr;    // max |v| bits for the signed fixed point
+  unsigned long long* halo3 = nullptr;   // 3 shell buffers of the three-channel vector paint
+  uint32_t* done3 = nullptr;   // its 3 x ntiles face counters (zero between paints)
   double* partial = nullptr;   // chi^2 block partials
   double* d_loss = nullptr;
 };
@@ -123,6 +125,8 @@ void free_plan(fpm_plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->aspec);
   cudaFree(p->adj6);
+  cudaFree(p->halo3);
+  cudaFree(p->done3);
   cudaFree(p->gS);
   cudaFree(p->gF);
   cudaFree(p->vbuf);
@@ -675,6 +679,12 @@ static int ensure_adjoint(fpm_plan* p) {
       (rc = dalloc(p, &p->partial, CHI_PARTIALS)) || (rc = dalloc(p, &p->d_loss, 1)) ||
       (rc = dalloc(p, &p->gF, 3 * p->M)))
     return rc;
+  if (p->pc.tile_done && p->pc.ntiles <= VEC3_MAX_TILES) {   // the three-channel vector paint
+    if ((rc = dalloc(p, &p->halo3, 3 * paint_halo_elems(p->pc.ntiles))) ||
+        (rc = dalloc(p, &p->done3, 3 * (size_t)p->pc.ntiles)))
+      return rc;
+    if (cudaMemset(p->done3, 0, 3 * sizeof(uint32_t) * p->pc.ntiles) != cudaSuccess) return FPM_ECUDA;
+  }
   return FPM_OK;
 }
 
@@ -721,8 +731,9 @@ static int force_jt_impl(fpm_plan* p, const PaintCtx& c, const float* x, float* 
                          const float* F, cudaStream_t s, bool vmax_ready = false, NextDriftKick next = {},
                          bool* fused = nullptr) {
   if (fused) *fused = false;
-  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s,
-                [&] { return launch_paint_vec(c, x, v, vk, p->vmax, p->gF, s, vmax_ready); }));
+  const int nvec = (vmax_ready ? 0 : 1) + (c.tile_done && p->halo3 ? 1 : (c.tile_done ? 3 : 6));
+  FPM_TRY(timed(p, FPM_K_PAINT, nvec, s,
+                [&] { return launch_paint_vec(c, x, v, vk, p->vmax, p->gF, s, vmax_ready, p->halo3, p->done3); }));
   FPM_TRY(force_adj_impl(p, p->gF, p->rho, s));
   if (next.idr >= 0 && fused) {
     FPM_TRY(timed(p, FPM_K_READOUT, 1, s, [&] {
@@ -788,8 +799,8 @@ int fpm_readout_adj(fpm_plan* p, const float* F, const float* dx, const float* g
   FPM_TRY(timed(p, FPM_K_KEYS, 1, s, [&] { return launch_keys(c, dx, s); }));
   FPM_TRY(timed(p, FPM_K_SCAN, 1, s, [&] { return launch_scan(c, s); }));
   FPM_TRY(timed(p, FPM_K_SCATTER, 1, s, [&] { return launch_scatter(c, s); }));
-  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done ? 4 : 7, s,
-                [&] { return launch_paint_vec(c, dx, g_f, KScale{}, p->vmax, g_F, s); }));
+  FPM_TRY(timed(p, FPM_K_PAINT, c.tile_done && p->halo3 ? 2 : (c.tile_done ? 4 : 7), s,
+                [&] { return launch_paint_vec(c, dx, g_f, KScale{}, p->vmax, g_F, s, false, p->halo3, p->done3); }));
   return timed(p, FPM_K_READOUT, 1, s,
                [&] { return launch_gather_adj(c, dx, nullptr, F, false, g_f, g_dx, false, s); });
 }

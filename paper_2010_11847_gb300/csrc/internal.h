@@ -124,8 +124,17 @@ int launch_gather_adj(const PaintCtx& c, const float* dx, const float* g_rho, co
                       const float* v, float* g_dx, bool accumulate, cudaStream_t s, KScale vk = KScale{});
 // The three channels v_i = K v[ch][i] (K from vk); vmax_ready: *vmax
 // already holds max |K v| (bit pattern), e.g. from launch_gather_adj_dk.
+// With halo3 (3 shell buffers of paint_halo_elems) and done3 (3 x ntiles
+// face counters, zero between paints) meshes of at most VEC3_MAX_TILES
+// tiles (nc <= 128) have their channels painted by one launch, side by side
+// (one channel's 512 tiles alone leave most of the GPU idle: 128^3 forward
+// + adjoint 3.90 -> 3.63 ms); larger meshes, or without the buffers, take
+// one launch per channel on the plan's buffers (at 512^3 the side-by-side
+// launch measured slower, 4.53 vs 4.34 ms per reverse step).
+constexpr int VEC3_MAX_TILES = 512;
 int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, KScale vk, unsigned* vmax, float* out,
-                     cudaStream_t s, bool vmax_ready = false);
+                     cudaStream_t s, bool vmax_ready = false, unsigned long long* halo3 = nullptr,
+                     uint32_t* done3 = nullptr);
 // launch_gather_adj (accumulating, float4 force, brick lattices) with the
 // cotangent velocities v = K gp taken from the momentum cotangents gp (K
 // from vk), followed per particle by the next reverse step's drift and kick

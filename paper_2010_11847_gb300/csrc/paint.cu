@@ -567,27 +567,34 @@ __device__ __forceinline__ void body_halo_vec(const unsigned long long* __restri
 // Readout transpose for one channel: out_c = sum_i W(x_i - c) v_i (no
 // mass), v_i = K vch_i (vk), deterministic signed fixed point in units set
 // by max |v|.
+// With nch = 3 one launch paints the three channels: block b takes tile
+// b / 3 and channel b % 3 (the three blocks of a tile run side by side and
+// share the tile's items, cells and dx gathers through L2), each channel
+// with its own output, shell buffer and face counters (strides M, hstride,
+// ntiles); with nch = 1 the block paints channel 0 of the given pointers.
 __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restrict__ dx, size_t N,
                                                           const uint32_t* __restrict__ items,
                                                           const uint32_t* __restrict__ tile_start, Geom g,
-                                                          const float* __restrict__ vch, KScale vk,
+                                                          const float* __restrict__ v, KScale vk,
                                                           const unsigned* __restrict__ vmax,
-                                                          float* __restrict__ out,
-                                                          unsigned long long* __restrict__ halo,
+                                                          float* __restrict__ out_all,
+                                                          unsigned long long* __restrict__ halo_all,
                                                           const uint16_t* __restrict__ cells,
-                                                          uint32_t* __restrict__ done) {
+                                                          uint32_t* __restrict__ done_all, int nch, size_t M,
+                                                          size_t hstride) {
   __shared__ uint32_t lo[ACC], hi[ACC];
   __shared__ uint32_t sm[24];
-  const int nt = g.nt, nc = g.nc;
-  const int tile = blockIdx.x;
+  const int nt = g.nt;
+  const int tile = nch == 1 ? (int)blockIdx.x : (int)blockIdx.x / 3;
+  const float* __restrict__ vch = v + (blockIdx.x - tile * nch) * N;
   const int o[3] = {(tile / (nt * nt)) * TILE, ((tile / nt) % nt) * TILE, (tile % nt) * TILE};
   const uint32_t s0 = tile_start[tile], s1 = tile_start[tile + 1];
   const float scale = signed_scale(*vmax), inv = 1.f / scale;
   const float K = kscale(vk);
   for (int k = threadIdx.x; k < ACC; k += blockDim.x) lo[k] = hi[k] = 0u;
   __syncthreads();
-  auto deposit = [&](const int* l, const float* t, float v) {
-    const float vs = (K * v) * scale;
+  auto deposit = [&](const int* l, const float* t, float vi) {
+    const float vs = (K * vi) * scale;
     const int base = (l[0] * TILE1 + l[1]) * TILE1 + l[2];
     const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
 #pragma unroll
@@ -630,6 +637,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_paint_vec(const float* __restric
     }
   }
   __syncthreads();
+  // this block's channel's output, shell buffer and face counters
+  const int ch = blockIdx.x - tile * nch;
+  float* out = out_all + ch * M;
+  unsigned long long* halo = halo_all + ch * hstride;
+  uint32_t* done = done_all ? done_all + (size_t)ch * nt * nt * nt : nullptr;
   paint_writeout_conv(Acc32{lo, hi}, o, tile, g, out, halo,
                       [inv](unsigned long long v) { return from_fix_signed((long long)v, inv); });
   if (done) faces_last(done, halo, g, tile, sm, [&](int u) { body_halo_vec(halo, g, inv, out, sm, u); });
@@ -715,15 +727,21 @@ int launch_gather_adj_dk(const PaintCtx& c, const float* dx, const float* g_rho,
 }
 
 int launch_paint_vec(const PaintCtx& c, const float* dx, const float* v, KScale vk, unsigned* vmax, float* out,
-                     cudaStream_t s, bool vmax_ready) {
+                     cudaStream_t s, bool vmax_ready, unsigned long long* halo3, uint32_t* done3) {
   if (!vmax_ready) {
     FPM_CUDA_TRY(cudaMemsetAsync(vmax, 0, sizeof(unsigned), s));
     k_maxabs<<<1024, 256, 0, s>>>(v, vk, 3 * c.N, vmax);
     FPM_CUDA_TRY(cudaGetLastError());
   }
+  if (halo3 && done3 && c.tile_done && c.ntiles <= VEC3_MAX_TILES) {
+    k_paint_vec<<<3 * c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v, vk, vmax, out, halo3,
+                                                    cells_of(c), done3, 3, c.M, paint_halo_elems(c.ntiles));
+    FPM_CUDA_TRY(cudaGetLastError());
+    return FPM_OK;
+  }
   for (int ch = 0; ch < 3; ++ch) {
     k_paint_vec<<<c.ntiles, PB_THREADS, 0, s>>>(dx, c.N, c.items, c.tile_start, c.g, v + ch * c.N, vk, vmax,
-                                                out + ch * c.M, c.halo, cells_of(c), c.tile_done);
+                                                out + ch * c.M, c.halo, cells_of(c), c.tile_done, 1, 0, 0);
     FPM_CUDA_TRY(cudaGetLastError());
     if (!c.tile_done) {
       k_halo_vec<<<c.ntiles, 768, 0, s>>>(c.halo, c.g, vmax, out + ch * c.M);

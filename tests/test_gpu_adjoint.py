@@ -58,7 +58,9 @@ def test_force_adj_matches_oracle(torch_mod):
     assert rel_l2(got, O.force_adj(gF.astype(np.float64), OM)) < 1e-5
 
 
-@pytest.mark.parametrize("np_,nc", [(32, 32), (32, 64)])
+# (32, 32), (32, 64): the three cotangent channels painted by one launch;
+# (64, 256): one launch per channel (meshes of more than 512 tiles)
+@pytest.mark.parametrize("np_,nc", [(32, 32), (32, 64), (64, 256)])
 def test_paint_and_readout_adj_match_oracle(torch_mod, np_, nc):
     torch = torch_mod
     pl = plan(np_, nc)
