@@ -104,9 +104,12 @@ def test_lpt_and_linear_field_adj_match_oracle(torch_mod, order):
     assert rel_l2(gw.cpu().numpy(), O.linear_field_adj(rG, box, COSMO)) < 1e-5
 
 
-def test_kdk_adj_matches_oracle_given_the_same_checkpoints(torch_mod):
+# 32^3: the velocity cotangents stored by a drift-kick kernel; 64^3 (a
+# lattice of whole 4 x 16 x 64 bricks): read as K g_p by the paint and the
+# gather, which also applies the next step's drift and kick transposes
+@pytest.mark.parametrize("n,nc,box", [(32, 32, 100.0), (64, 64, 200.0)])
+def test_kdk_adj_matches_oracle_given_the_same_checkpoints(torch_mod, n, nc, box):
     torch = torch_mod
-    n, nc, box = 32, 32, 100.0
     stages = np.linspace(0.1, 0.7, 4)
     pl = plan(n, nc, box)
     lk = O.linear_field(inputs.white_noise(n, 5), box, COSMO)
@@ -213,7 +216,7 @@ def test_differentiable_config_gradient(torch_mod):
     assert np.linalg.norm(fds[3e-2] - ad) / np.linalg.norm(ad) < VOXEL_FD_BOUND
 
 
-@pytest.mark.parametrize("np_,nc,reverse", [(32, 64, True), (32, 32, True), (48, 96, False)])
+@pytest.mark.parametrize("np_,nc,reverse", [(32, 64, True), (32, 32, True), (64, 64, True), (48, 96, False)])
 def test_force_checkpoints_give_the_same_bits(torch_mod, np_, nc, reverse):
     """Keeping the forward's force meshes and tile buckets (fckpt) changes
     nothing but the work: the same forward state and checkpoints (float4 and
